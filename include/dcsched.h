@@ -1,0 +1,197 @@
+/*
+ * dcsched.h -- C-ABI of the GPU network-aware multi-criteria container
+ * scheduler (arXiv 1909.07673, "Network-Aware Container Scheduling in
+ * Multi-Tenant Data Center").
+ *
+ * One dc_t is one data center G^s(N^s, E^s) (Sec. II-A): a k-port fat-tree
+ * (Sec. IV-B.1) with k^3/4 identical hosts, integer residual CPU and memory
+ * per host and integer residual bandwidth per undirected link, kept resident
+ * in GPU memory.  Tenant requests Req(N^c, E^c) (Sec. II-A, Table I) are
+ * submitted in arrival order; dc_schedule places them first-come first-served
+ * on the GPU: for each pod, every host is ranked by TOPSIS (Sec. V-C) or AHP
+ * (Sec. V-B, Eqs. 9-10), the best host (lowest index on ties) is taken, and
+ * CPU, memory and bandwidth along widest shortest paths (Sec. V-D) are
+ * committed (Eqs. 4-8).  A request whose pod cannot be placed is rejected
+ * and leaves no trace.  dc_query returns the maps M_c (container -> host)
+ * and M_ec (link -> path) of Sec. II-A.
+ *
+ * Conventions (every entry point):
+ *   - Returns DC_OK (0) or a negative DC_E_* code; never throws or aborts.
+ *   - Every pointer argument is a HOST pointer unless stated otherwise.  The
+ *     caller owns all input and output arrays; inputs are copied before the
+ *     call returns and the library keeps no pointer to them.
+ *   - int32 arrays are dense and in the caller's index order.
+ *   - A dc_t (and every dc_t passed together to one call) is used by one
+ *     host thread at a time.
+ *   - CUDA errors are reported as DC_E_CUDA; a kernel that reports a bad
+ *     input or an exhausted wait returns DC_E_INVAL / DC_E_TIMEOUT and the
+ *     instance must be destroyed.
+ *
+ * Limits (checked, DC_E_INVAL beyond): k even, 2 <= k <= 32 (one thread
+ * block holds the whole data center on chip); host_cpu, host_mem <= 65535;
+ * link_mbps <= 2^21 - 1; at most 2^18 links per request.
+ *
+ * Link numbering (also used by dc_query_state and dc_result.path), one
+ * undirected residual per link (the u < v storage of Sec. V-D):
+ *   host h hangs from edge switch e = h / (k/2) of pod p = e / (k/2);
+ *   host-edge link of host h            : h
+ *   edge switch e -- aggregation a      : H + e*(k/2) + a
+ *   aggregation a of pod p -- core (a,c): 2H + (p*(k/2) + a)*(k/2) + c
+ * with H = k^3/4 hosts and 3H links in total.
+ */
+#ifndef DCSCHED_H
+#define DCSCHED_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  DC_OK = 0,
+  DC_E_INVAL = -1,    /* bad argument, bad request, limit exceeded */
+  DC_E_NOMEM = -2,    /* host or device allocation failed */
+  DC_E_CUDA = -3,     /* a CUDA call failed (sticky per context) */
+  DC_E_TIMEOUT = -4,  /* a bounded device wait ran out */
+  DC_E_NOTFOUND = -5, /* unknown request id */
+  DC_E_BUSY = -6      /* state does not allow the call (e.g. stale plan) */
+};
+
+/* ranking method (Sec. V) */
+enum { DC_TOPSIS = 0, DC_AHP = 1 };
+/* AHP pairwise rule: RATIO a_ij = (x_i+1)/(x_j+1) (consistent, default);
+ * DIFF the difference rule of Sec. V-B made reciprocal:
+ * a_ij = d, 1/|d| or 1 for d = x_i - x_j > 0, < 0, = 0. */
+enum { DC_PAIR_RATIO = 0, DC_PAIR_DIFF = 1 };
+/* request status */
+enum { DC_PENDING = 0, DC_ACCEPTED = 1, DC_REJECTED = 2 };
+/* dc_schedule flags */
+enum { DC_SCHED_SYNC = 0, DC_SCHED_ASYNC = 1 };
+/* dc_query_state fields */
+enum {
+  DC_FIELD_FREE_CPU = 0, /* [H] residual CPU units */
+  DC_FIELD_FREE_MEM = 1, /* [H] residual memory units */
+  DC_FIELD_CTR = 2,      /* [H] containers hosted */
+  DC_FIELD_PRE = 3,      /* [H] 1 if the host was pre-loaded at dc_create */
+  DC_FIELD_LINK_RES = 4  /* [3H] residual bandwidth per link (numbering above) */
+};
+
+typedef struct dc_t dc_t;
+typedef struct dc_plan dc_plan;
+
+typedef struct {
+  int32_t k;          /* fat-tree port count (Sec. IV-B.1) */
+  int32_t host_cpu;   /* CPU units of every host, c^s_u[CPU] */
+  int32_t host_mem;   /* memory units of every host, c^s_u[RAM] */
+  int32_t link_mbps;  /* bandwidth of every link, bw^s_uv */
+  int32_t n_criteria; /* 4: free CPU, free memory, active flag f_u, uplink
+                         residual bw^s_u (Sec. V, Table IV order);
+                         6: plus path bandwidth and locality to the pod's
+                         already-placed neighbours */
+  int32_t method;     /* DC_TOPSIS | DC_AHP */
+  int32_t pair_rule;  /* DC_PAIR_RATIO | DC_PAIR_DIFF (AHP only) */
+  double weights[6];  /* criteria weights W (Sec. V-A, Table IV), >= 0, sum > 0 */
+  const int32_t* pre_cpu;  /* [H] CPU already used, or NULL */
+  const int32_t* pre_mem;  /* [H] memory already used, or NULL */
+  const int32_t* pre_link; /* [3H] bandwidth already used, or NULL */
+} dc_config;
+
+typedef struct {
+  int32_t n_containers, n_edges;
+  /* [n_containers]: c^min/c^max (Table I) and pod id; pod ids are dense
+   * 0..P-1; containers without a pod are singleton pods. */
+  const int32_t *cpu_min, *cpu_max, *mem_min, *mem_max, *pod;
+  /* [n_edges]: undirected container links i -- j (src != dst) with
+   * [bw^min, bw^max] (Table I). */
+  const int32_t *src, *dst, *bw_min, *bw_max;
+} dc_request;
+
+typedef struct {
+  int32_t status;      /* DC_ACCEPTED | DC_REJECTED | DC_PENDING */
+  int32_t n_decisions; /* pod rankings performed (each over all H hosts) */
+  int32_t* host;       /* [n_containers] M_c, -1 when rejected */
+  int32_t* cpu;        /* [n_containers] allocated CPU, c^a_i */
+  int32_t* mem;        /* [n_containers] allocated memory */
+  int32_t* bw;         /* [n_edges] allocated bandwidth bw^a_ij */
+  int32_t* path;       /* [6 * n_edges] M_ec: link ids from the host of src
+                          to the host of dst, -1 padded */
+  double* pod_score;   /* [n_pods] FP64 score of the chosen host (oracle
+                          arithmetic), -1 for pods not placed */
+} dc_result;
+
+/* Creates a data center on the current CUDA device.  cuda_stream: the
+ * cudaStream_t (as void*) every operation of this instance is ordered on;
+ * NULL = the legacy default stream.  Copies the pre-load arrays.
+ * DC_E_INVAL on a bad config or pre-load above capacity. */
+int dc_create(const dc_config* cfg, void* cuda_stream, dc_t** out);
+
+/* Frees every host and device resource of the instance (waits for its work). */
+void dc_destroy(dc_t* dc);
+
+/* Appends a request to the instance's FCFS queue (Sec. II-A request; FCFS =
+ * submission order).  Validates and copies the arrays; no device work.
+ * *req_id receives 0, 1, 2, ... in submission order. */
+int dc_submit_request(dc_t* dc, const dc_request* req, int64_t* req_id);
+
+/* Queues the departure of request req_id after everything submitted so far:
+ * when reached, an accepted request returns its CPU, memory and bandwidth
+ * (a rejected one returns nothing).  DC_E_NOTFOUND for an unknown id,
+ * DC_E_BUSY if it was already queued for release. */
+int dc_release(dc_t* dc, int64_t req_id);
+
+/* Schedules every queued operation of n instances in one batched launch
+ * (instances run concurrently; each instance's operations run in FCFS
+ * order).  DC_SCHED_SYNC waits for completion; DC_SCHED_ASYNC returns once
+ * the work is enqueued (dc_query then reports DC_PENDING until done). */
+int dc_schedule(dc_t* const* dcs, int32_t n, int32_t flags);
+
+/* Copies the result of request req_id into caller arrays sized from the
+ * request (any output pointer may be NULL).  Waits for an in-flight
+ * schedule only if wait != 0; otherwise out->status = DC_PENDING when not
+ * finished.  DC_E_NOTFOUND for an unknown id. */
+int dc_query(dc_t* dc, int64_t req_id, dc_result* out, int32_t wait);
+
+/* Copies one state field (see DC_FIELD_*) into out[len]; waits for the
+ * instance's queued work first.  DC_E_INVAL if len is too small. */
+int dc_query_state(dc_t* dc, int32_t field, int32_t* out, int64_t len);
+
+/* Ranks every host for pod `pod` of `req` on the current state without
+ * committing anything: host_of[n_containers] gives the hosts of containers
+ * of earlier pods (-1 elsewhere).  Outputs (host arrays, each may be NULL):
+ * feasible[H] (0/1), score32[H] (FP32 fast-path score, NaN if not viable),
+ * score64[H] (FP64 score with the oracle's arithmetic, NaN if not viable),
+ * crit[H * n_criteria] (criteria, row-major per host).  Returns the number
+ * of viable hosts (>= 0) or an error code. */
+int dc_rank_hosts(dc_t* dc, const dc_request* req, int32_t pod, const int32_t* host_of,
+                  int32_t* feasible, float* score32, double* score64, int32_t* crit);
+
+/* Restores the state given at dc_create and forgets every request. */
+int dc_reset(dc_t* dc);
+
+/* --- plans: the scheduling launch of dc_schedule, prepared once ---------
+ * dc_plan_create stages the queued operations of n instances on the device
+ * (request inputs host -> device) and prepares the batched launch; with
+ * DC_PLAN_GRAPH it is captured in a CUDA graph; with DC_PLAN_RESET each
+ * launch first restores every instance's dc_create state, so the plan can be
+ * replayed.  dc_plan_launch enqueues the launch on `cuda_stream` (device
+ * work only, no host copies); dc_plan_collect waits for it and makes the
+ * results available to dc_query.  A plan is stale (DC_E_BUSY) once one of
+ * its instances gets new requests or is reset. */
+enum { DC_PLAN_GRAPH = 1, DC_PLAN_RESET = 2 };
+int dc_plan_create(dc_t* const* dcs, int32_t n, int32_t flags, dc_plan** out);
+int dc_plan_launch(dc_plan* plan, void* cuda_stream);
+int dc_plan_collect(dc_plan* plan);
+/* Totals of the last collected launch: pod decisions and host rankings
+ * (decisions x hosts), and the number of kernels one launch runs. */
+int dc_plan_stats(dc_plan* plan, int64_t* decisions, int64_t* host_rankings,
+                  int32_t* kernels_per_launch);
+void dc_plan_destroy(dc_plan* plan);
+
+/* Human-readable text of an error code (static storage). */
+const char* dc_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

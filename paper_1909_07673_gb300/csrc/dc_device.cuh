@@ -1,0 +1,1090 @@
+// dc_device.cuh -- sm_103a device code of the network-aware multi-criteria
+// container scheduler (arXiv 1909.07673, Sec. V).
+//
+// One thread block owns one data center for the whole launch: the packed
+// host state (free CPU | free memory, container count, residual of every
+// link) is loaded into shared memory once, every queued operation of the
+// instance is processed in FCFS order, and the state is written back at the
+// end.  A pod decision is a chain of block-wide phases:
+//
+//   setup    (warp 0)  pod demand (sums of c^min / c^max), the pod's links to
+//                      containers of earlier pods, per-edge-switch and
+//                      per-pod neighbour counts, a host -> link-count hash [a1]
+//   tables   (block)   for every edge switch e, the smallest bottleneck
+//                      min(uplink(v), best switch path e -> edge(v)) over the
+//                      placed neighbours v and the smallest slack against
+//                      their bw^min, each with its host and the runner-up
+//                      over other hosts (a neighbour host excludes itself) [a2, a3]
+//   stats    (block)   viability and criteria of every host; exact integer
+//                      column statistics over the viable hosts (count, sum,
+//                      sum of squares, max, min) by warp redux + one
+//                      cross-warp pass; FP32 per-column constants         [a4]
+//   score    (block)   FP32 score of every viable host (TOPSIS closeness or
+//                      AHP global priority), kept in registers            [a5]
+//   pick     (block)   top-2 argmax (lowest index on ties); certification:
+//                      hosts within a relative guard band of the maximum
+//                      are re-scored with the FP64 expression of the
+//                      oracle unless they carry the leader's criteria     [a6]
+//   commit   (warp 0)  widest shortest path per link to a placed neighbour
+//                      (warp-parallel over the (a, c) candidates), bandwidth
+//                      and capacity reservation; on failure undo, mask the
+//                      host and pick again (scores are not recomputed)    [a7, a8]
+//
+// At the end of each request the FP64 scores of the chosen hosts are
+// evaluated in parallel (one thread per pod) from per-pod decision records,
+// with exactly the operations and rounding of the oracle.
+//
+// There is no dense contraction anywhere, so no tensor-core path: the work
+// is integer and FP32 arithmetic over shared memory, bounded by the
+// dependency chain of the pod decisions of one data center and, across data
+// centers, by the SM count.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cfloat>
+#include <climits>
+#include <cstdint>
+
+#include "../../include/dcsched.h"
+#include "dc_internal.h"
+
+namespace dcs {
+
+// ---------------------------------------------------------------- context
+
+struct Ctx {
+  // instance
+  int32_t k, half, H, E, C, method, link_mbps;
+  unsigned long long mh;  // ceil(2^32 / half): x / half == (x * mh) >> 32
+  double W[kMaxC], L1[kMaxC];
+  float Wf[kMaxC], L1f[kMaxC];
+  int4* scr_pe;
+  // request
+  int64_t c_off, e_off, p_off, l_off;
+  int32_t n_c, n_e, n_p;
+  const int32_t* pc;  // pod -> container range (shared or global)
+  const int32_t* pe;  // pod -> link range
+  int32_t* hof;       // container -> host (shared copy, or the global output)
+  // pod
+  long long dmin_cpu, dmax_cpu, dmin_mem, dmax_mem;
+  int32_t size, npe;
+  int32_t need1, need1h, need2;
+  int32_t hash_ok;
+  // column statistics over the viable hosts
+  int32_t n;
+  long long S1[kMaxC], S2[kMaxC];
+  int32_t mx[kMaxC], mn[kMaxC];
+  // per-column constants: FP32 for the fast path, FP64 (oracle arithmetic)
+  // computed only when the guard band needs re-scoring
+  float qf[kMaxC], invTf[kMaxC];
+  double norm[kMaxC], Ap[kMaxC], An[kMaxC], Td[kMaxC];
+  // selection
+  float m1, m2;
+  int32_t idx1;
+  int32_t winner;
+  int32_t commit_ok;
+  int32_t ndec;
+  int32_t placed;
+};
+
+struct Sm {
+  Ctx* c;
+  uint32_t* cm;   // [H] free cpu | free mem << 16
+  int32_t* ctr;   // [H] container count | kPreBit
+  int32_t* res;   // [3H] link residuals (numbering of dcsched.h)
+  int32_t *T1, *T1h, *T2, *S1, *S1h, *S2, *Be;  // [E] per edge switch
+  int32_t* Cp;    // [k] per pod
+  int32_t* G;     // [kChunk * k * half]
+  uint32_t* tmark;    // [B] bit j of word t: host t + j*B hosts a neighbour
+  uint32_t* trymask;  // [B] bit j of word t: host t + j*B failed a commit
+  int32_t *hkey, *hcnt;  // [kHash]
+  long long* red64;
+  int32_t* red32;
+  unsigned char* sel;
+  int32_t *st_pc, *st_pe, *st_hof;
+};
+
+static __device__ __forceinline__ Sm carve(unsigned char* base, int k, int B) {
+  SmemLayout L = smem_layout(k, B, sizeof(Ctx));
+  Sm s;
+  s.c = reinterpret_cast<Ctx*>(base + L.ctx);
+  s.cm = reinterpret_cast<uint32_t*>(base + L.cm);
+  s.ctr = reinterpret_cast<int32_t*>(base + L.ctr);
+  s.res = reinterpret_cast<int32_t*>(base + L.res);
+  const int E = k * k / 2;
+  int32_t* t = reinterpret_cast<int32_t*>(base + L.tab);
+  s.T1 = t; s.T1h = t + E; s.T2 = t + 2 * E; s.S1 = t + 3 * E; s.S1h = t + 4 * E;
+  s.S2 = t + 5 * E; s.Be = t + 6 * E;
+  s.Cp = reinterpret_cast<int32_t*>(base + L.cp);
+  s.G = reinterpret_cast<int32_t*>(base + L.g);
+  s.tmark = reinterpret_cast<uint32_t*>(base + L.tmark);
+  s.trymask = reinterpret_cast<uint32_t*>(base + L.trymask);
+  s.hkey = reinterpret_cast<int32_t*>(base + L.hkey);
+  s.hcnt = reinterpret_cast<int32_t*>(base + L.hcnt);
+  s.red64 = reinterpret_cast<long long*>(base + L.red64);
+  s.red32 = reinterpret_cast<int32_t*>(base + L.red32);
+  s.sel = base + L.sel;
+  s.st_pc = reinterpret_cast<int32_t*>(base + L.st_pc);
+  s.st_pe = reinterpret_cast<int32_t*>(base + L.st_pe);
+  s.st_hof = reinterpret_cast<int32_t*>(base + L.st_hof);
+  return s;
+}
+
+// ---------------------------------------------------------------- helpers
+
+static __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+static __device__ __forceinline__ int imin(int a, int b) { return a < b ? a : b; }
+static __device__ __forceinline__ int imax(int a, int b) { return a > b ? a : b; }
+static __device__ __forceinline__ int div_half(const Ctx& c, int x) {
+  return (int)(((unsigned long long)(unsigned)x * c.mh) >> 32);
+}
+
+// link ids (numbering of dcsched.h)
+static __device__ __forceinline__ int l_ea(const Ctx& c, int e, int a) { return c.H + e * c.half + a; }
+static __device__ __forceinline__ int l_ac(const Ctx& c, int p, int a, int cc) {
+  return 2 * c.H + (p * c.half + a) * c.half + cc;
+}
+
+// "top-2 by host" folds: value 1 with its host, and the best value over
+// entries whose host differs from host 1.
+struct Top2 { int v1, h1, v2; };
+static __device__ __forceinline__ Top2 min2_combine(Top2 a, Top2 b) {
+  if (a.h1 == b.h1) return {imin(a.v1, b.v1), a.h1, imin(a.v2, b.v2)};
+  if (a.v1 <= b.v1) return {a.v1, a.h1, imin(a.v2, b.v1)};
+  return {b.v1, b.h1, imin(b.v2, a.v1)};
+}
+static __device__ __forceinline__ Top2 max2_combine(Top2 a, Top2 b) {
+  if (a.h1 == b.h1) return {imax(a.v1, b.v1), a.h1, imax(a.v2, b.v2)};
+  if (a.v1 >= b.v1) return {a.v1, a.h1, imax(a.v2, b.v1)};
+  return {b.v1, b.h1, imax(b.v2, a.v1)};
+}
+
+static __device__ __forceinline__ uint32_t hash_host(int h) {
+  return ((uint32_t)h * 2654435761u) >> 22;  // 10 bits = kHash slots
+}
+
+// number of the pod's links whose placed end is on host u
+static __device__ int peer_links_on(const Sm& s, int u) {
+  const Ctx& c = *s.c;
+  if (c.hash_ok) {
+    uint32_t slot = hash_host(u);
+    for (int p = 0; p < kHash; ++p) {
+      const int key = s.hkey[slot];
+      if (key == u) return s.hcnt[slot];
+      if (key == -1) return 0;
+      slot = (slot + 1) & (kHash - 1);
+    }
+    return 0;
+  }
+  int n = 0;
+  for (int i = 0; i < c.npe; ++i) n += (c.scr_pe[i].y == u);
+  return n;
+}
+
+// Criteria of host u (integers, all benefit criteria) and its viability.
+// c0 free CPU, c1 free memory, c2 active flag f_u, c3 uplink residual;
+// with 6 criteria c4 = smallest bottleneck to the pod's placed neighbours
+// (link capacity for a neighbour on u itself, c3 without neighbours) and
+// c5 = sum over the pod's links to placed neighbours of (6 - hops).
+template <int B>
+static __device__ __forceinline__ bool host_crit(const Sm& s, int u, int32_t* x) {
+  const Ctx& c = *s.c;
+  const uint32_t cm = s.cm[u];
+  const int cpu = (int)(cm & 0xffffu), mem = (int)(cm >> 16);
+  const int ctr = s.ctr[u];
+  const int up = s.res[u];
+  bool f = cpu >= c.dmin_cpu && mem >= c.dmin_mem;
+  x[0] = cpu;
+  x[1] = mem;
+  x[2] = ((ctr & kCtrMask) > 0 || (ctr & kPreBit)) ? 1 : 0;
+  x[3] = up;
+  int c4 = up, c5 = 0;
+  if (c.npe > 0) {
+    const int e = div_half(c, u), p = div_half(c, e);
+    const bool isp = (s.tmark[u % B] >> (u / B)) & 1u;
+    const int Tx = (isp && s.T1h[e] == u) ? s.T2[e] : s.T1[e];
+    const int Sx = (isp && s.S1h[e] == u) ? s.S2[e] : s.S1[e];
+    const int Nx = (isp && c.need1h == u) ? c.need2 : c.need1;
+    f = f && up >= Nx && Sx >= 0;
+    c4 = (Tx == kInf) ? c.link_mbps : imin(up, Tx);
+    const int A = isp ? peer_links_on(s, u) : 0;
+    const int Bn = s.Be[e], Cn = s.Cp[p];
+    c5 = 6 * A + 4 * (Bn - A) + 2 * (Cn - Bn);
+  }
+  if (c.C == 6) {
+    x[4] = c4;
+    x[5] = c5;
+  }
+  return f;
+}
+
+// Out-of-line copy for the rare certification paths (keeps code size down).
+template <int B>
+static __device__ __noinline__ bool host_crit_slow(const Sm& s, int u, int32_t* x) {
+  return host_crit<B>(s, u, x);
+}
+
+static __device__ __forceinline__ bool same_vec(const int32_t* a, const int32_t* b, int C) {
+  bool eq = true;
+#pragma unroll
+  for (int v = 0; v < kMaxC; ++v)
+    if (v < C) eq = eq && (a[v] == b[v]);
+  return eq;
+}
+
+// FP32 fast-path score.  TOPSIS: differences to the ideal / anti-ideal are
+// formed exactly in integers, scaled by q_v = W_v / sqrt(sum x^2) and
+// accumulated with FMA; relative error <= 19 * 2^-24 against the exact
+// closeness.  AHP RATIO: sum_v L1_v (x_v + 1) / T_v, error <= 11 * 2^-24.
+static __device__ __forceinline__ float score32(const Ctx& c, const int32_t* x) {
+  if (c.method == DC_TOPSIS) {
+    float dp = 0.f, dn = 0.f;
+#pragma unroll
+    for (int v = 0; v < kMaxC; ++v) {
+      if (v < c.C) {
+        const float a = (float)(x[v] - c.mx[v]) * c.qf[v];
+        const float b = (float)(x[v] - c.mn[v]) * c.qf[v];
+        dp = __fmaf_rn(a, a, dp);
+        dn = __fmaf_rn(b, b, dn);
+      }
+    }
+    const float Dp = __fsqrt_rn(dp), Dn = __fsqrt_rn(dn);
+    const float s = __fadd_rn(Dp, Dn);
+    return s == 0.f ? 1.f : __fdiv_rn(Dn, s);
+  }
+  float acc = 0.f;
+#pragma unroll
+  for (int v = 0; v < kMaxC; ++v)
+    if (v < c.C) acc = __fmaf_rn(c.L1f[v], __fmul_rn((float)(x[v] + 1), c.invTf[v]), acc);
+  return acc;
+}
+
+// FP64 per-column constants with the oracle's operations: TOPSIS norm
+// sqrt(sum x^2) and the weighted normalised extremes A+ / A- (the weighted
+// normalised value is monotone in x, so its max / min over the viable hosts
+// are those of the integer max / min); AHP RATIO T = sum (x + 1).
+static __device__ __forceinline__ void fp64_column(double W, int method, long long S1, long long S2,
+                                                   int mx, int mn, int n, double* norm, double* Ap,
+                                                   double* An, double* Td) {
+  if (method == DC_TOPSIS) {
+    const double nrm = S2 > 0 ? __dsqrt_rn((double)S2) : 0.0;
+    *norm = nrm;
+    *Ap = nrm > 0.0 ? __dmul_rn(__ddiv_rn((double)mx, nrm), W) : 0.0;
+    *An = nrm > 0.0 ? __dmul_rn(__ddiv_rn((double)mn, nrm), W) : 0.0;
+  } else {
+    *Td = (double)(S1 + n);
+  }
+}
+
+// FP64 score with exactly the operations, order and rounding of the oracle
+// (each step one IEEE binary64 operation rounded to nearest, no FMA).
+static __device__ __noinline__ double score64(int method, int C, const double* W, const double* L1,
+                                              const double* norm, const double* Ap,
+                                              const double* An, const double* Td,
+                                              const int32_t* x) {
+  if (method == DC_TOPSIS) {
+    double dp = 0.0, dn = 0.0;
+    for (int v = 0; v < C; ++v) {
+      const double r = norm[v] > 0.0 ? __ddiv_rn((double)x[v], norm[v]) : 0.0;
+      const double t = __dmul_rn(r, W[v]);
+      const double a = __dsub_rn(t, Ap[v]);
+      dp = __dadd_rn(dp, __dmul_rn(a, a));
+      const double b = __dsub_rn(t, An[v]);
+      dn = __dadd_rn(dn, __dmul_rn(b, b));
+    }
+    const double Dp = __dsqrt_rn(dp), Dn = __dsqrt_rn(dn);
+    const double s = __dadd_rn(Dp, Dn);
+    return s == 0.0 ? 1.0 : __ddiv_rn(Dn, s);
+  }
+  double acc = 0.0;
+  for (int v = 0; v < C; ++v)
+    acc = __dadd_rn(acc, __dmul_rn(L1[v], __ddiv_rn((double)(x[v] + 1), Td[v])));
+  return acc;
+}
+
+// ---------------------------------------------------------------- phases
+
+// a1: pod demand and the pod's links to containers of earlier pods (warp 0).
+static __device__ void pod_setup_warp(const Sm& s, const InstDev& I, int g) {
+  Ctx& c = *s.c;
+  const int lane = lane_id();
+  const int32_t c0 = c.pc[g], c1 = c.pc[g + 1];
+  long long dmin_c = 0, dmax_c = 0, dmin_m = 0, dmax_m = 0;
+  for (int pos = c0 + lane; pos < c1; pos += 32) {
+    const int4 q = I.c_lay[c.c_off + pos];
+    dmin_c += q.y & 0xffff;
+    dmax_c += (unsigned)q.y >> 16;
+    dmin_m += q.z & 0xffff;
+    dmax_m += (unsigned)q.z >> 16;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    dmin_c += __shfl_xor_sync(0xffffffffu, dmin_c, o);
+    dmax_c += __shfl_xor_sync(0xffffffffu, dmax_c, o);
+    dmin_m += __shfl_xor_sync(0xffffffffu, dmin_m, o);
+    dmax_m += __shfl_xor_sync(0xffffffffu, dmax_m, o);
+  }
+  const int32_t e0 = c.pe[g], e1 = c.pe[g + 1];
+  int npe = 0;
+  bool hash_ok = true;
+  Top2 nd = {-1, -1, -1};
+  for (int base = e0; base < e1; base += 32) {
+    const int pos = base + lane;
+    bool peer = false;
+    int4 q = make_int4(0, 0, 0, 0);
+    int hv = 0;
+    if (pos < e1) {
+      q = I.e_lay[c.e_off + pos];
+      peer = !(q.x & kLinkIntra);
+      if (peer) hv = c.hof[q.y];
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, peer);
+    if (peer) {
+      const int slot = npe + __popc(m & ((1u << lane) - 1u));
+      c.scr_pe[slot] = make_int4(q.x, hv, q.z, q.w);
+      const int ev = div_half(c, hv);
+      atomicAdd(&s.Be[ev], 1);
+      atomicAdd(&s.Cp[div_half(c, ev)], 1);
+      uint32_t h = hash_host(hv);
+      bool ins = false;
+      for (int p = 0; p < kHash / 2; ++p) {  // bounded probing
+        const int old = atomicCAS(&s.hkey[h], -1, hv);
+        if (old == -1 || old == hv) {
+          atomicAdd(&s.hcnt[h], 1);
+          ins = true;
+          break;
+        }
+        h = (h + 1) & (kHash - 1);
+      }
+      if (!ins) hash_ok = false;
+      nd = max2_combine(nd, Top2{q.z, hv, -1});
+    }
+    npe += __popc(m);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    Top2 other = {__shfl_xor_sync(0xffffffffu, nd.v1, o), __shfl_xor_sync(0xffffffffu, nd.h1, o),
+                  __shfl_xor_sync(0xffffffffu, nd.v2, o)};
+    nd = max2_combine(nd, other);
+  }
+  hash_ok = __all_sync(0xffffffffu, hash_ok);
+  if (lane == 0) {
+    c.dmin_cpu = dmin_c;
+    c.dmax_cpu = dmax_c;
+    c.dmin_mem = dmin_m;
+    c.dmax_mem = dmax_m;
+    c.size = c1 - c0;
+    c.npe = npe;
+    c.need1 = nd.v1;
+    c.need1h = nd.h1;
+    c.need2 = nd.v2;
+    c.hash_ok = hash_ok ? 1 : 0;
+  }
+}
+
+// marks the hosts of placed neighbours (block-wide, after setup)
+template <int B>
+static __device__ void mark_peers(const Sm& s) {
+  const Ctx& c = *s.c;
+  for (int i = threadIdx.x; i < c.npe; i += B) {
+    const int hv = c.scr_pe[i].y;
+    atomicOr(&s.tmark[hv % B], 1u << (hv / B));
+  }
+}
+
+// a2/a3 tables: T'_v[e] = min(uplink(v), best switch-path bottleneck from
+// edge switch e to edge(v)) folded over the pod's placed neighbours v.
+template <int B>
+static __device__ void build_tables(const Sm& s) {
+  const Ctx& c = *s.c;
+  const int tid = threadIdx.x;
+  const int half = c.half, k = c.k, E = c.E;
+  for (int base = 0; base < c.npe; base += kChunk) {
+    const int nch = imin(kChunk, c.npe - base);
+    // G[i][p][a] = max_c min(ac(p, a, c), ac(pod(v_i), a, c))
+    const int per = k * half;
+    for (int idx = tid; idx < nch * per; idx += B) {
+      const int i = idx / per, rem = idx - i * per;
+      const int p = div_half(c, rem), a = rem - p * half;
+      const int pv = div_half(c, div_half(c, c.scr_pe[base + i].y));
+      int m = -1;
+      for (int cc = 0; cc < half; ++cc)
+        m = imax(m, imin(s.res[l_ac(c, p, a, cc)], s.res[l_ac(c, pv, a, cc)]));
+      s.G[idx] = m;
+    }
+    __syncthreads();
+    for (int e = tid; e < E; e += B) {
+      Top2 t = {s.T1[e], s.T1h[e], s.T2[e]};
+      Top2 sl = {s.S1[e], s.S1h[e], s.S2[e]};
+      const int pe_ = div_half(c, e);
+      for (int i = 0; i < nch; ++i) {
+        const int4 q = c.scr_pe[base + i];
+        const int v = q.y, need = q.z;
+        const int ev = div_half(c, v), pv = div_half(c, ev);
+        int mid;
+        if (e == ev) {
+          mid = kInf;
+        } else if (pe_ == pv) {
+          mid = -1;
+          for (int a = 0; a < half; ++a)
+            mid = imax(mid, imin(s.res[l_ea(c, e, a)], s.res[l_ea(c, ev, a)]));
+        } else {
+          mid = -1;
+          const int32_t* Gi = s.G + i * per + pe_ * half;
+          for (int a = 0; a < half; ++a)
+            mid = imax(mid, imin(imin(s.res[l_ea(c, e, a)], s.res[l_ea(c, ev, a)]), Gi[a]));
+        }
+        const int T = imin(s.res[v], mid);
+        t = min2_combine(t, Top2{T, v, kInf});
+        sl = min2_combine(sl, Top2{T - need, v, kInf});
+      }
+      s.T1[e] = t.v1; s.T1h[e] = t.h1; s.T2[e] = t.v2;
+      s.S1[e] = sl.v1; s.S1h[e] = sl.h1; s.S2[e] = sl.v2;
+    }
+    __syncthreads();
+  }
+}
+
+// a4: exact column statistics over the viable hosts and FP32 constants.
+template <int B>
+static __device__ void column_stats(const Sm& s) {
+  Ctx& c = *s.c;
+  const int tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
+  constexpr int NW = B / 32;
+  const int C = c.C;
+  uint32_t cnt = 0;
+  uint32_t s1[kMaxC];
+  unsigned long long s2[kMaxC];
+  int mx[kMaxC], mn[kMaxC];
+#pragma unroll
+  for (int v = 0; v < kMaxC; ++v) { s1[v] = 0; s2[v] = 0; mx[v] = INT_MIN; mn[v] = INT_MAX; }
+  for (int u = tid; u < c.H; u += B) {
+    int32_t x[kMaxC];
+    if (host_crit<B>(s, u, x)) {
+      ++cnt;
+#pragma unroll
+      for (int v = 0; v < kMaxC; ++v) {
+        if (v < C) {
+          s1[v] += (uint32_t)x[v];
+          s2[v] += (unsigned long long)((long long)x[v] * x[v]);
+          mx[v] = imax(mx[v], x[v]);
+          mn[v] = imin(mn[v], x[v]);
+        }
+      }
+    }
+  }
+  // warp level: 32-bit redux (sum of squares split in 24-bit halves)
+  const uint32_t wc = __reduce_add_sync(0xffffffffu, cnt);
+#pragma unroll
+  for (int v = 0; v < kMaxC; ++v) {
+    if (v < C) {
+      const uint32_t a = __reduce_add_sync(0xffffffffu, s1[v]);
+      const uint32_t lo = __reduce_add_sync(0xffffffffu, (uint32_t)(s2[v] & 0xffffffull));
+      const uint32_t hi = __reduce_add_sync(0xffffffffu, (uint32_t)(s2[v] >> 24));
+      const int M = __reduce_max_sync(0xffffffffu, mx[v]);
+      const int N = __reduce_min_sync(0xffffffffu, mn[v]);
+      if (lane == 0) {
+        s.red64[w * 2 * kMaxC + v] = (long long)a;
+        s.red64[w * 2 * kMaxC + kMaxC + v] = ((long long)hi << 24) + (long long)lo;
+        s.red32[w * (2 * kMaxC + 1) + v] = M;
+        s.red32[w * (2 * kMaxC + 1) + kMaxC + v] = N;
+      }
+    }
+  }
+  if (lane == 0) s.red32[w * (2 * kMaxC + 1) + 2 * kMaxC] = (int)wc;
+  __syncthreads();
+  // block level: warp w reduces criteria w, w + NW, ... over the NW partials
+  for (int v = w; v < C; v += NW) {
+    long long a = 0, b = 0;
+    int M = INT_MIN, N = INT_MAX, n = 0;
+    if (lane < NW) {
+      a = s.red64[lane * 2 * kMaxC + v];
+      b = s.red64[lane * 2 * kMaxC + kMaxC + v];
+      M = s.red32[lane * (2 * kMaxC + 1) + v];
+      N = s.red32[lane * (2 * kMaxC + 1) + kMaxC + v];
+      n = s.red32[lane * (2 * kMaxC + 1) + 2 * kMaxC];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      b += __shfl_xor_sync(0xffffffffu, b, o);
+    }
+    M = __reduce_max_sync(0xffffffffu, M);
+    N = __reduce_min_sync(0xffffffffu, N);
+    n = (int)__reduce_add_sync(0xffffffffu, (uint32_t)n);
+    if (lane == 0) {
+      c.S1[v] = a;
+      c.S2[v] = b;
+      c.mx[v] = M;
+      c.mn[v] = N;
+      if (v == 0) c.n = n;
+      // FP32 constants: q_v = W_v / sqrt(sum x^2); 1 / sum (x + 1)
+      c.qf[v] = b > 0 ? __fmul_rn(c.Wf[v], __frsqrt_rn((float)b)) : 0.f;
+      c.invTf[v] = __frcp_rn((float)(a + n));
+    }
+  }
+  __syncthreads();
+}
+
+// FP64 constants of every column (block-wide; rare path).
+template <int B>
+static __device__ void column_fp64(const Sm& s) {
+  Ctx& c = *s.c;
+  constexpr int NW = B / 32;
+  const int w = threadIdx.x >> 5;
+  if (lane_id() == 0)
+    for (int v = w; v < c.C; v += NW)
+      fp64_column(c.W[v], c.method, c.S1[v], c.S2[v], c.mx[v], c.mn[v], c.n, &c.norm[v], &c.Ap[v],
+                  &c.An[v], &c.Td[v]);
+  __syncthreads();
+}
+
+// a5: FP32 scores of the viable hosts owned by this thread (-1 otherwise).
+template <int B, int HPT>
+static __device__ __forceinline__ void score_pass(const Sm& s, float* sc) {
+  const Ctx& c = *s.c;
+  const int tid = threadIdx.x;
+#pragma unroll
+  for (int j = 0; j < HPT; ++j) {
+    sc[j] = -1.f;
+    const int u = tid + j * B;
+    if (u < c.H) {
+      int32_t x[kMaxC];
+      if (host_crit<B>(s, u, x)) sc[j] = score32(c, x);
+    }
+  }
+}
+
+// block-wide (max, lowest index, second distinct max) over FP32 scores
+struct Sel { float m1; int idx; float m2; };
+static __device__ __forceinline__ Sel sel_combine(Sel a, Sel b) {
+  if (a.m1 > b.m1) return {a.m1, a.idx, fmaxf(a.m2, b.m1)};
+  if (a.m1 < b.m1) return {b.m1, b.idx, fmaxf(b.m2, a.m1)};
+  return {a.m1, imin(a.idx, b.idx), fmaxf(a.m2, b.m2)};
+}
+struct Sel64 { double s; int idx; };
+static __device__ __forceinline__ Sel64 sel64_combine(Sel64 a, Sel64 b) {
+  if (a.s > b.s) return a;
+  if (a.s < b.s) return b;
+  return {a.s, imin(a.idx, b.idx)};
+}
+
+// a6: argmax over sc[] (hosts that failed a commit excluded) and
+// certification.  Sets c.winner (-1 when no candidate remains).
+template <int B, int HPT>
+static __device__ void pick_host(const Sm& s, const float* sc) {
+  Ctx& c = *s.c;
+  const int tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
+  constexpr int NW = B / 32;
+  const uint32_t tried = s.trymask[tid];
+  Sel me = {-1.f, INT_MAX, -1.f};
+#pragma unroll
+  for (int j = 0; j < HPT; ++j)
+    if (sc[j] >= 0.f && !((tried >> j) & 1u)) me = sel_combine(me, Sel{sc[j], tid + j * B, -1.f});
+  for (int o = 16; o > 0; o >>= 1) {
+    Sel t = {__shfl_xor_sync(0xffffffffu, me.m1, o), __shfl_xor_sync(0xffffffffu, me.idx, o),
+             __shfl_xor_sync(0xffffffffu, me.m2, o)};
+    me = sel_combine(me, t);
+  }
+  Sel* ws = reinterpret_cast<Sel*>(s.sel);
+  if (lane == 0) ws[w] = me;
+  __syncthreads();
+  if (w == 0) {
+    Sel t = lane < NW ? ws[lane] : Sel{-1.f, INT_MAX, -1.f};
+    for (int o = 16; o > 0; o >>= 1) {
+      Sel q = {__shfl_xor_sync(0xffffffffu, t.m1, o), __shfl_xor_sync(0xffffffffu, t.idx, o),
+               __shfl_xor_sync(0xffffffffu, t.m2, o)};
+      t = sel_combine(t, q);
+    }
+    if (lane == 0) {
+      c.m1 = t.m1;
+      c.idx1 = t.idx;
+      c.m2 = t.m2;
+      c.winner = t.m1 < 0.f ? -1 : t.idx;
+    }
+  }
+  __syncthreads();
+  const float m1 = c.m1;
+  if (m1 < 0.f) return;  // nothing viable left (c.winner == -1)
+  const int idx1 = c.idx1;
+  // guard band: every host whose FP64 score can reach the maximum has an
+  // FP32 score >= m1 * (1 - 2^-16) (the FP32 error is below 2e-6 relative)
+  const float thr = __fsub_rn(m1, m1 * 0x1p-16f);
+  bool need_x1 = false;
+#pragma unroll
+  for (int j = 0; j < HPT; ++j)
+    need_x1 = need_x1 || (sc[j] >= thr && !((tried >> j) & 1u) && tid + j * B != idx1);
+  int32_t x1[kMaxC];
+  if (need_x1) host_crit_slow<B>(s, idx1, x1);
+  bool full = !(c.m2 < thr);
+  if (!full) {
+    // only hosts with exactly the leader's score are in the band: they are
+    // certified if they all carry the leader's criteria vector
+    bool mism = false;
+#pragma unroll
+    for (int j = 0; j < HPT; ++j) {
+      const int u = tid + j * B;
+      if (sc[j] == m1 && !((tried >> j) & 1u) && u != idx1) {
+        int32_t x[kMaxC];
+        host_crit_slow<B>(s, u, x);
+        mism = mism || !same_vec(x, x1, c.C);
+      }
+    }
+    full = __syncthreads_or(mism);
+  }
+  if (!full) return;  // c.winner = idx1
+  // FP64 re-scoring of the band with the oracle's arithmetic; hosts carrying
+  // the leader's vector are represented by the leader (same score, lower
+  // index)
+  column_fp64<B>(s);
+  Sel64 b = {-1.0, INT_MAX};
+#pragma unroll
+  for (int j = 0; j < HPT; ++j) {
+    const int u = tid + j * B;
+    if (sc[j] >= thr && !((tried >> j) & 1u)) {
+      int32_t x[kMaxC];
+      host_crit_slow<B>(s, u, x);
+      if (u == idx1 || !same_vec(x, x1, c.C))
+        b = sel64_combine(b, Sel64{score64(c.method, c.C, c.W, c.L1, c.norm, c.Ap, c.An, c.Td, x), u});
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    Sel64 q = {__shfl_xor_sync(0xffffffffu, b.s, o), __shfl_xor_sync(0xffffffffu, b.idx, o)};
+    b = sel64_combine(b, q);
+  }
+  Sel64* ws64 = reinterpret_cast<Sel64*>(s.sel);
+  if (lane == 0) ws64[w] = b;
+  __syncthreads();
+  if (w == 0) {
+    Sel64 t = lane < NW ? ws64[lane] : Sel64{-1.0, INT_MAX};
+    for (int o = 16; o > 0; o >>= 1) {
+      Sel64 q = {__shfl_xor_sync(0xffffffffu, t.s, o), __shfl_xor_sync(0xffffffffu, t.idx, o)};
+      t = sel64_combine(t, q);
+    }
+    if (lane == 0) c.winner = t.idx;
+  }
+  __syncthreads();
+}
+
+// Widest shortest path between hosts hs != ht (warp-wide; every lane gets
+// the result).  Ties: lowest aggregation index a, then lowest core index c.
+struct PathSel { int b, idx; };
+static __device__ __forceinline__ PathSel path_combine(PathSel a, PathSel b) {
+  if (a.b > b.b) return a;
+  if (a.b < b.b) return b;
+  return {a.b, imin(a.idx, b.idx)};
+}
+
+static __device__ int widest_path_warp(const Sm& s, int hs, int ht, int* links, int* nl) {
+  const Ctx& c = *s.c;
+  const int lane = lane_id();
+  const int half = c.half;
+  const int es = div_half(c, hs), et = div_half(c, ht), ps = div_half(c, es), pt = div_half(c, et);
+  const int us = s.res[hs], ut = s.res[ht];
+  if (es == et) {
+    links[0] = hs; links[1] = ht; *nl = 2;
+    return imin(us, ut);
+  }
+  PathSel best = {-1, INT_MAX};
+  const bool same_pod = ps == pt;
+  const int ncand = same_pod ? half : half * half;
+  for (int i = lane; i < ncand; i += 32) {
+    const int a = same_pod ? i : div_half(c, i), cc = same_pod ? 0 : i - a * half;
+    int b = imin(imin(us, ut), imin(s.res[l_ea(c, es, a)], s.res[l_ea(c, et, a)]));
+    if (!same_pod) b = imin(b, imin(s.res[l_ac(c, ps, a, cc)], s.res[l_ac(c, pt, a, cc)]));
+    best = path_combine(best, PathSel{b, i});
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    PathSel q = {__shfl_xor_sync(0xffffffffu, best.b, o), __shfl_xor_sync(0xffffffffu, best.idx, o)};
+    best = path_combine(best, q);
+  }
+  const int a = same_pod ? best.idx : div_half(c, best.idx), cc = same_pod ? 0 : best.idx - a * half;
+  if (same_pod) {
+    links[0] = hs; links[1] = l_ea(c, es, a); links[2] = l_ea(c, et, a); links[3] = ht;
+    *nl = 4;
+  } else {
+    links[0] = hs; links[1] = l_ea(c, es, a); links[2] = l_ac(c, ps, a, cc);
+    links[3] = l_ac(c, pt, a, cc); links[4] = l_ea(c, et, a); links[5] = ht;
+    *nl = 6;
+  }
+  return best.b;
+}
+
+// a7/a8: commit of pod g on c.winner (warp 0).  Sets c.commit_ok.
+template <int B>
+static __device__ void commit_warp(const Sm& s, const InstDev& I, int g) {
+  Ctx& c = *s.c;
+  const int lane = lane_id();
+  const int u = c.winner;
+  // decision record for the FP64 score: the criteria of u before any of
+  // this pod's reservations (rewritten by a later attempt if this one fails)
+  if (lane == 0) {
+    PodLog* L = I.scr_log + g;
+    int32_t x[kMaxC];
+    host_crit_slow<B>(s, u, x);
+    for (int v = 0; v < kMaxC; ++v) {
+      L->x[v] = v < c.C ? x[v] : 0;
+      L->mx[v] = c.mx[v];
+      L->mn[v] = c.mn[v];
+      L->S1[v] = c.S1[v];
+      L->S2[v] = c.S2[v];
+    }
+    L->n = c.n;
+  }
+  __syncwarp();
+  int done = 0;  // peer links committed so far
+  bool ok = true;
+  for (int base = 0; base < c.npe && ok; base += 32) {
+    int4 mine = make_int4(0, 0, 0, 0);
+    if (base + lane < c.npe) mine = c.scr_pe[base + lane];
+    const int cnt = imin(32, c.npe - base);
+    for (int i = 0; i < cnt; ++i) {
+      const int ew = __shfl_sync(0xffffffffu, mine.x, i);
+      const int v = __shfl_sync(0xffffffffu, mine.y, i);
+      const int bmin = __shfl_sync(0xffffffffu, mine.z, i);
+      const int bmax = __shfl_sync(0xffffffffu, mine.w, i);
+      const int e = ew & kLinkIndex;
+      const bool mine_src = (ew & kLinkMineSrc) != 0;
+      const int hs = mine_src ? u : v, ht = mine_src ? v : u;
+      int32_t* path = I.o_path + (c.e_off + e) * 6;
+      if (hs == ht) {
+        if (lane == 0) I.o_bw[c.e_off + e] = bmax;
+      } else {
+        int links[6], nl = 0;
+        const int b = widest_path_warp(s, hs, ht, links, &nl);
+        if (b < bmin) {
+          ok = false;
+          break;
+        }
+        const int amount = b >= bmax ? bmax : bmin;
+        if (lane == 0) {
+          for (int j = 0; j < nl; ++j) {
+            s.res[links[j]] -= amount;
+            path[j] = links[j];
+          }
+          I.o_bw[c.e_off + e] = amount;
+        }
+      }
+      ++done;
+      __syncwarp();
+    }
+  }
+  if (!ok) {
+    // undo this pod's reservations (links committed before the failure)
+    for (int i = lane; i < done; i += 32) {
+      const int e = c.scr_pe[i].x & kLinkIndex;
+      int32_t* path = I.o_path + (c.e_off + e) * 6;
+      const int bw = I.o_bw[c.e_off + e];
+      for (int j = 0; j < 6; ++j) {
+        const int l = path[j];
+        if (l >= 0) atomicAdd(&s.res[l], bw);
+        path[j] = -1;
+      }
+      I.o_bw[c.e_off + e] = 0;
+    }
+    __syncwarp();
+    if (lane == 0) {
+      atomicOr(&s.trymask[u % B], 1u << (u / B));
+      c.commit_ok = 0;
+    }
+    return;
+  }
+  // capacity (Eqs. 4, 6): per resource c^max for every container when the
+  // host has room for the sum of maxima, else c^min
+  const uint32_t cm = s.cm[u];
+  const bool take_cpu_max = (long long)(cm & 0xffffu) >= c.dmax_cpu;
+  const bool take_mem_max = (long long)(cm >> 16) >= c.dmax_mem;
+  const int32_t c0 = c.pc[g], c1 = c.pc[g + 1];
+  uint32_t used_c = 0, used_m = 0;
+  for (int pos = c0 + lane; pos < c1; pos += 32) {
+    const int4 q = I.c_lay[c.c_off + pos];
+    const int a = take_cpu_max ? ((unsigned)q.y >> 16) : (q.y & 0xffff);
+    const int m = take_mem_max ? ((unsigned)q.z >> 16) : (q.z & 0xffff);
+    I.o_host[c.c_off + q.x] = u;
+    I.o_cpu[c.c_off + q.x] = a;
+    I.o_mem[c.c_off + q.x] = m;
+    c.hof[q.x] = u;
+    used_c += a;
+    used_m += m;
+  }
+  used_c = __reduce_add_sync(0xffffffffu, used_c);
+  used_m = __reduce_add_sync(0xffffffffu, used_m);
+  if (lane == 0) {
+    s.cm[u] = cm - (used_c | (used_m << 16));
+    s.ctr[u] += c.size;
+    c.commit_ok = 1;
+  }
+  __syncwarp();
+}
+
+// Gives back everything the request holds (rollback of a rejected request
+// or a departure).  Block-wide; clears the outputs when `clear`.
+template <int B>
+static __device__ void give_back(const Sm& s, const InstDev& I, int64_t c_off, int n_c,
+                                 int64_t e_off, int n_e, bool clear) {
+  const int tid = threadIdx.x;
+  for (int i = tid; i < n_c; i += B) {
+    const int h = I.o_host[c_off + i];
+    if (h >= 0) {
+      atomicAdd(&s.cm[h], (uint32_t)I.o_cpu[c_off + i] | ((uint32_t)I.o_mem[c_off + i] << 16));
+      atomicSub(&s.ctr[h], 1);
+      if (clear) {
+        I.o_host[c_off + i] = -1;
+        I.o_cpu[c_off + i] = 0;
+        I.o_mem[c_off + i] = 0;
+      }
+    }
+  }
+  for (int e = tid; e < n_e; e += B) {
+    int32_t* path = I.o_path + (e_off + e) * 6;
+    const int bw = I.o_bw[e_off + e];
+    for (int j = 0; j < 6; ++j) {
+      const int l = path[j];
+      if (l >= 0) {
+        atomicAdd(&s.res[l], bw);
+        if (clear) path[j] = -1;
+      }
+    }
+    if (clear) I.o_bw[e_off + e] = 0;
+  }
+  __syncthreads();
+}
+
+// Per-pod table reset (block-wide, before setup).
+template <int B>
+static __device__ void reset_tables(const Sm& s) {
+  const Ctx& c = *s.c;
+  const int tid = threadIdx.x;
+  for (int e = tid; e < c.E; e += B) {
+    s.Be[e] = 0;
+    s.T1[e] = kInf; s.T1h[e] = -1; s.T2[e] = kInf;
+    s.S1[e] = kInf; s.S1h[e] = -1; s.S2[e] = kInf;
+  }
+  for (int p = tid; p < c.k; p += B) s.Cp[p] = 0;
+  for (int h = tid; h < kHash; h += B) {
+    s.hkey[h] = -1;
+    s.hcnt[h] = 0;
+  }
+}
+
+template <int B>
+static __device__ void load_instance(const Sm& s, const InstDev& I) {
+  Ctx& c = *s.c;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    c.k = I.k; c.half = I.half; c.H = I.H; c.E = I.E; c.C = I.C; c.method = I.method;
+    c.link_mbps = I.link_mbps;
+    c.mh = ((1ull << 32) + (unsigned long long)I.half - 1) / (unsigned long long)I.half;
+    c.scr_pe = I.scr_pe;
+    for (int v = 0; v < kMaxC; ++v) {
+      c.W[v] = v < I.C ? I.W[v] : 0.0;
+      c.L1[v] = v < I.C ? I.L1[v] : 0.0;
+      c.Wf[v] = (float)c.W[v];
+      c.L1f[v] = (float)c.L1[v];
+    }
+  }
+  for (int u = tid; u < I.H; u += B) {
+    s.cm[u] = (uint32_t)I.cpu[u] | ((uint32_t)I.mem[u] << 16);
+    s.ctr[u] = I.ctr[u] | (I.pre[u] ? kPreBit : 0);
+  }
+  for (int l = tid; l < 3 * I.H; l += B) s.res[l] = I.res[l];
+  s.tmark[tid] = 0;
+  s.trymask[tid] = 0;
+  __syncthreads();
+}
+
+template <int B>
+static __device__ void store_instance(const Sm& s, const InstDev& I) {
+  const int tid = threadIdx.x;
+  for (int u = tid; u < I.H; u += B) {
+    const uint32_t cm = s.cm[u];
+    I.cpu[u] = (int32_t)(cm & 0xffffu);
+    I.mem[u] = (int32_t)(cm >> 16);
+    I.ctr[u] = s.ctr[u] & kCtrMask;
+  }
+  for (int l = tid; l < 3 * I.H; l += B) I.res[l] = s.res[l];
+}
+
+// Request header, and its index arrays staged in shared memory when they
+// fit (pod ranges; host of every container, -1 until placed).
+template <int B>
+static __device__ void load_request(const Sm& s, const InstDev& I, int r, const int32_t* host_of) {
+  Ctx& c = *s.c;
+  const int tid = threadIdx.x;
+  const ReqRec q = I.reqs[r];
+  const bool stage_p = q.n_p + 1 <= kStageP + 1;
+  const bool stage_c = q.n_c <= kStageC;
+  if (tid == 0) {
+    c.c_off = q.c_off; c.e_off = q.e_off; c.p_off = q.p_off; c.l_off = q.l_off;
+    c.n_c = q.n_c; c.n_e = q.n_e; c.n_p = q.n_p;
+    c.pc = stage_p ? s.st_pc : I.p_coff + q.l_off;
+    c.pe = stage_p ? s.st_pe : I.p_eoff + q.l_off;
+    c.hof = stage_c ? s.st_hof : I.o_host + q.c_off;
+    c.ndec = 0;
+    c.placed = 0;
+  }
+  if (stage_p)
+    for (int i = tid; i <= q.n_p; i += B) {
+      s.st_pc[i] = I.p_coff[q.l_off + i];
+      s.st_pe[i] = I.p_eoff[q.l_off + i];
+    }
+  if (stage_c)
+    for (int i = tid; i < q.n_c; i += B) s.st_hof[i] = host_of ? host_of[i] : -1;
+  __syncthreads();
+}
+
+// One pod decision (a1..a8).  Returns true when the pod is placed.
+template <int B, int HPT>
+static __device__ bool decide_pod(const Sm& s, const InstDev& I, int g) {
+  Ctx& c = *s.c;
+  const int tid = threadIdx.x;
+  reset_tables<B>(s);
+  __syncthreads();
+  if (tid < 32) pod_setup_warp(s, I, g);
+  __syncthreads();
+  if (c.npe > 0) {
+    mark_peers<B>(s);
+    build_tables<B>(s);  // starts and ends with a barrier
+  }
+  column_stats<B>(s);
+  float sc[HPT];
+  score_pass<B, HPT>(s, sc);
+  bool placed = false;
+  for (;;) {
+    pick_host<B, HPT>(s, sc);
+    if (c.winner < 0) break;
+    if (tid < 32) commit_warp<B>(s, I, g);
+    __syncthreads();
+    if (c.commit_ok) {
+      placed = true;
+      break;
+    }
+  }
+  s.tmark[tid] = 0;
+  s.trymask[tid] = 0;
+  if (tid == 0) c.ndec += 1;
+  __syncthreads();
+  return placed;
+}
+
+// FP64 scores of the chosen hosts of pods [0, n_placed) from their decision
+// records (one thread per pod); -1 stays for the others.
+template <int B>
+static __device__ void pod_scores(const Sm& s, const InstDev& I, int n_placed) {
+  const Ctx& c = *s.c;
+  for (int g = threadIdx.x; g < n_placed; g += B) {
+    const PodLog* L = I.scr_log + g;
+    double norm[kMaxC], Ap[kMaxC], An[kMaxC], Td[kMaxC];
+    int32_t x[kMaxC];
+    for (int v = 0; v < c.C; ++v) {
+      fp64_column(c.W[v], c.method, L->S1[v], L->S2[v], L->mx[v], L->mn[v], L->n, &norm[v], &Ap[v],
+                  &An[v], &Td[v]);
+      x[v] = L->x[v];
+    }
+    I.o_score[c.p_off + g] = score64(c.method, c.C, c.W, c.L1, norm, Ap, An, Td, x);
+  }
+}
+
+template <int B, int HPT>
+static __device__ void schedule_request(const Sm& s, const InstDev& I, int r) {
+  Ctx& c = *s.c;
+  const int tid = threadIdx.x;
+  load_request<B>(s, I, r, nullptr);
+  const int64_t c_off = c.c_off, e_off = c.e_off, p_off = c.p_off;
+  const int n_c = c.n_c, n_e = c.n_e, n_p = c.n_p;
+  for (int i = tid; i < n_c; i += B) {
+    I.o_host[c_off + i] = -1;
+    I.o_cpu[c_off + i] = 0;
+    I.o_mem[c_off + i] = 0;
+  }
+  for (int e = tid; e < n_e; e += B) {
+    I.o_bw[e_off + e] = 0;
+    for (int j = 0; j < 6; ++j) I.o_path[(e_off + e) * 6 + j] = -1;
+  }
+  for (int p = tid; p < n_p; p += B) I.o_score[p_off + p] = -1.0;
+  __syncthreads();
+  int g = 0;
+  for (; g < n_p; ++g)
+    if (!decide_pod<B, HPT>(s, I, g)) break;
+  const bool accepted = g == n_p;
+  if (accepted) {
+    // links inside a pod use no network link and get bw^max
+    for (int e = tid; e < n_e; e += B) {
+      const int4 q = I.e_lay[e_off + e];
+      if (q.x & kLinkIntra) I.o_bw[e_off + (q.x & kLinkIndex)] = q.w;
+    }
+  } else {
+    give_back<B>(s, I, c_off, n_c, e_off, n_e, true);
+  }
+  pod_scores<B>(s, I, g);
+  if (tid == 0) {
+    I.o_status[r] = accepted ? DC_ACCEPTED : DC_REJECTED;
+    I.o_ndec[r] = c.ndec;
+    atomicAdd(&I.counters[0], (unsigned long long)c.ndec);
+    atomicAdd(&I.counters[1], (unsigned long long)c.ndec * (unsigned long long)c.H);
+  }
+  __syncthreads();
+}
+
+template <int B, int HPT>
+__global__ void __launch_bounds__(B, 1) k_schedule(const InstDev* __restrict__ insts) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const InstDev& I = insts[blockIdx.x];
+  const Sm s = carve(smem, I.k, B);
+  load_instance<B>(s, I);
+  for (int op = 0; op < I.n_ops; ++op) {
+    const int w = I.ops[op];
+    const int r = w & (kOpRelease - 1);
+    if (w & kOpRelease) {
+      const int st = I.o_status[r];
+      if ((st & 0xff) == DC_ACCEPTED && !(st & kReleased)) {
+        const ReqRec q = I.reqs[r];
+        give_back<B>(s, I, q.c_off, q.n_c, q.e_off, q.n_e, false);
+        if (threadIdx.x == 0) I.o_status[r] = st | kReleased;
+      }
+    } else {
+      schedule_request<B, HPT>(s, I, r);
+    }
+    __syncthreads();
+  }
+  store_instance<B>(s, I);
+}
+
+// What-if ranking of pod `g` of request `r` with the given host_of, no
+// commit.  Writes per-host viability, criteria and both scores.
+template <int B, int HPT>
+__global__ void __launch_bounds__(B, 1) k_rank(const InstDev* __restrict__ inst, int r, int g,
+                                              const int32_t* __restrict__ host_of,
+                                              int32_t* feas, float* s32, double* s64,
+                                              int32_t* crit, int32_t* nviable) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const InstDev& I = *inst;
+  const Sm s = carve(smem, I.k, B);
+  load_instance<B>(s, I);
+  load_request<B>(s, I, r, host_of);
+  if (s.c->hof != s.st_hof) {
+    // request too large to stage: the global host_of is read directly
+    if (threadIdx.x == 0) s.c->hof = const_cast<int32_t*>(host_of);
+    __syncthreads();
+  }
+  reset_tables<B>(s);
+  __syncthreads();
+  if (threadIdx.x < 32) pod_setup_warp(s, I, g);
+  __syncthreads();
+  if (s.c->npe > 0) {
+    mark_peers<B>(s);
+    build_tables<B>(s);
+  }
+  column_stats<B>(s);
+  column_fp64<B>(s);
+  const Ctx& c = *s.c;
+  for (int u = threadIdx.x; u < c.H; u += B) {
+    int32_t x[kMaxC];
+    const bool f = host_crit<B>(s, u, x);
+    feas[u] = f ? 1 : 0;
+    s32[u] = f ? score32(c, x) : __int_as_float(0x7fc00000);
+    s64[u] = f ? score64(c.method, c.C, c.W, c.L1, c.norm, c.Ap, c.An, c.Td, x)
+               : __longlong_as_double(0x7ff8000000000000ll);
+    for (int v = 0; v < c.C; ++v) crit[(int64_t)u * c.C + v] = x[v];
+  }
+  if (threadIdx.x == 0) *nviable = c.n;
+}
+
+}  // namespace dcs

@@ -1,0 +1,137 @@
+// dc_internal.h -- structures shared by the host runtime (dc_runtime.cu) and
+// the scheduling kernels (dc_kernels.cu).  Not part of the public ABI.
+#pragma once
+#include <vector_types.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#if defined(__CUDACC__)
+#define DC_HD __host__ __device__
+#else
+#define DC_HD
+#endif
+
+namespace dcs {
+
+constexpr int kMaxC = 6;
+constexpr int32_t kInf = 0x7fffffff;
+// container-count word of a host: low 30 bits count, bit 30 = pre-loaded
+constexpr int32_t kPreBit = 1 << 30;
+constexpr int32_t kCtrMask = kPreBit - 1;
+// request status word: DC_ACCEPTED / DC_REJECTED, | kReleased once released
+constexpr int32_t kReleased = 0x100;
+// operation word: request index, | kOpRelease for a departure
+constexpr int32_t kOpRelease = 1 << 30;
+// peer-link word in scratch: link index, | kPeSrc when the pod holds the src end
+constexpr int32_t kPeSrc = 1 << 30;
+constexpr int32_t kMaxLinksPerRequest = 1 << 18;
+constexpr int32_t kMaxK = 32;
+constexpr int kChunk = 6;    // peer links per table-building chunk
+constexpr int kHash = 1024;  // slots of the per-pod peer-host hash table
+constexpr int kMaxBlock = 1024;
+
+// Link-record flags (e_lay[].x): the link joins two containers of one pod;
+// the pod being placed holds the link's src end.
+constexpr int32_t kLinkIntra = 1 << 29;
+constexpr int32_t kLinkMineSrc = 1 << 30;
+constexpr int32_t kLinkIndex = (1 << 29) - 1;
+// per-request index arrays staged in shared memory when they fit
+constexpr int kStageP = 1024;  // pods (+1 entries of the range arrays)
+constexpr int kStageC = 1024;  // containers
+
+// One request as stored on the device.  Its containers are c_lay[c_off ..
+// c_off + n_c) grouped by pod in index order, its links e_lay[e_off .. +n_e)
+// grouped by the later of their two pods in index order; pod g owns
+// c_lay[c_off + p_coff[l_off + g] .. p_coff[l_off + g + 1]) and likewise for
+// links with p_eoff.  Outputs use the request's own index order from c_off
+// / e_off; pod scores from p_off.
+struct ReqRec {
+  int64_t c_off, e_off, p_off, l_off;
+  int32_t n_c, n_e, n_p, pad;
+};
+
+// Per-pod decision record kept for the FP64 score of the chosen host: its
+// criteria and the column statistics of the viable hosts.
+struct PodLog {
+  int32_t x[kMaxC];
+  int32_t n;
+  int32_t mx[kMaxC], mn[kMaxC];
+  int32_t pad;
+  long long S1[kMaxC], S2[kMaxC];
+};
+
+// Everything one instance's thread block needs, in global memory.
+struct InstDev {
+  int32_t k, half, H, E, C, method, rule;
+  int32_t host_cpu, host_mem, link_mbps;
+  double W[kMaxC];
+  const double* L1;  // [C] AHP criteria priorities, FP64 (device)
+  // state (device)
+  int32_t *cpu, *mem, *ctr, *pre, *res;
+  // request store (device)
+  const ReqRec* reqs;
+  // c_lay: {container index, cpu_min | cpu_max << 16, mem_min | mem_max << 16, 0}
+  const int4* c_lay;
+  // e_lay: {link index | flags, container at the other end, bw_min, bw_max}
+  const int4* e_lay;
+  const int32_t *p_coff, *p_eoff;
+  int32_t *o_host, *o_cpu, *o_mem, *o_bw, *o_path, *o_status, *o_ndec;
+  double* o_score;
+  // operations of this launch, FCFS
+  const int32_t* ops;
+  int32_t n_ops;
+  int32_t scr_links;  // capacity of scr_pe, in links
+  int32_t scr_pods;   // capacity of scr_log, in pods
+  int4* scr_pe;       // peer links of the pod being placed
+  PodLog* scr_log;    // [pods of the current request]
+  int32_t* err;       // [1] 0 or a DC_E_* code
+  unsigned long long* counters;  // [2] pod decisions, host rankings (accumulated)
+};
+
+DC_HD inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Shared-memory layout of one scheduling block (bytes), see dc_kernels.cu.
+struct SmemLayout {
+  size_t ctx, cm, ctr, res, tab, cp, g, tmark, trymask, hkey, hcnt, red64, red32, sel;
+  size_t st_pc, st_pe, st_hof, total;
+};
+
+DC_HD inline SmemLayout smem_layout(int k, int block, size_t ctx_bytes) {
+  SmemLayout L;
+  const size_t H = (size_t)k * k * k / 4, E = (size_t)k * k / 2, half = (size_t)k / 2;
+  const size_t nw = (size_t)block / 32;
+  size_t o = 0;
+  L.ctx = o; o = align_up(o + ctx_bytes, 16);
+  L.cm = o; o = align_up(o + 4 * H, 16);
+  L.ctr = o; o = align_up(o + 4 * H, 16);
+  L.res = o; o = align_up(o + 12 * H, 16);
+  L.tab = o; o = align_up(o + 7 * 4 * E, 16);
+  L.cp = o; o = align_up(o + 4 * (size_t)k, 16);
+  L.g = o; o = align_up(o + 4 * (size_t)kChunk * k * half, 16);
+  L.tmark = o; o = align_up(o + 4 * (size_t)block, 16);
+  L.trymask = o; o = align_up(o + 4 * (size_t)block, 16);
+  L.hkey = o; o = align_up(o + 4 * (size_t)kHash, 16);
+  L.hcnt = o; o = align_up(o + 4 * (size_t)kHash, 16);
+  L.red64 = o; o = align_up(o + 8 * nw * 2 * kMaxC, 16);
+  L.red32 = o; o = align_up(o + 4 * nw * (2 * kMaxC + 1), 16);
+  L.sel = o; o = align_up(o + 16 * nw, 16);
+  L.st_pc = o; o = align_up(o + 4 * (size_t)(kStageP + 1), 16);
+  L.st_pe = o; o = align_up(o + 4 * (size_t)(kStageP + 1), 16);
+  L.st_hof = o; o = align_up(o + 4 * (size_t)kStageC, 16);
+  L.total = o;
+  return L;
+}
+
+// Launch wrappers (dc_kernels.cu); each returns DC_OK or DC_E_*.
+size_t ctx_bytes();
+int max_hosts_per_thread(int block);  // 0 for an unsupported block size
+int configure_kernels(size_t smem_max);
+// one block per descriptor of d_insts[0..n)
+int launch_schedule(int block, const InstDev* d_insts, int n, size_t smem, void* stream);
+int launch_rank(int block, const InstDev* d_inst, int32_t req, int32_t pod, const int32_t* host_of,
+                int32_t* feas, float* s32, double* s64, int32_t* crit, int32_t* nviable,
+                size_t smem, void* stream);
+int launch_weights(int C, int rule, const double* d_W, double* d_L1, void* stream);
+
+}  // namespace dcs

@@ -1,0 +1,942 @@
+// dc_runtime.cu -- host runtime behind the C-ABI of include/dcsched.h.
+//
+// An instance keeps its requests in pinned host arenas (appended by
+// dc_submit_request), mirrors them to device arenas when a launch is
+// prepared, and keeps its data-center state resident in device memory.  A
+// launch (dc_plan) groups the instances by fat-tree size, gives each group
+// one kernel with one thread block per instance (block size from the tuning
+// table), and runs the groups concurrently on forked streams; it can be
+// captured once in a CUDA graph and replayed.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/dcsched.h"
+#include "dc_internal.h"
+
+using namespace dcs;
+
+namespace {
+
+int cuda_rc(cudaError_t e) { return e == cudaSuccess ? DC_OK : DC_E_CUDA; }
+
+#define DC_TRY(expr)            \
+  do {                          \
+    int rc_ = (expr);           \
+    if (rc_ != DC_OK) return rc_; \
+  } while (0)
+#define DC_CUDA(expr) DC_TRY(cuda_rc(expr))
+
+// Growable pinned host array.
+template <class T>
+struct PinnedVec {
+  T* p = nullptr;
+  size_t n = 0, cap = 0;
+  int reserve(size_t m) {
+    if (m <= cap) return DC_OK;
+    size_t nc = std::max<size_t>(m, std::max<size_t>(1024, cap * 2));
+    T* q = nullptr;
+    if (cudaHostAlloc((void**)&q, nc * sizeof(T), cudaHostAllocDefault) != cudaSuccess)
+      return DC_E_NOMEM;
+    if (n) std::memcpy(q, p, n * sizeof(T));
+    if (p) cudaFreeHost(p);
+    p = q;
+    cap = nc;
+    return DC_OK;
+  }
+  int append(const T* src, size_t m) {
+    DC_TRY(reserve(n + m));
+    if (m) std::memcpy(p + n, src, m * sizeof(T));
+    n += m;
+    return DC_OK;
+  }
+  int resize(size_t m) {
+    DC_TRY(reserve(m));
+    n = m;
+    return DC_OK;
+  }
+  void release() {
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    n = cap = 0;
+  }
+};
+
+// Growable device array; growth keeps the first `keep` elements
+// (stream-ordered on the instance's stream).
+template <class T>
+struct DevVec {
+  T* p = nullptr;
+  size_t cap = 0;
+  int ensure(size_t m, size_t keep, cudaStream_t st) {
+    if (m <= cap) return DC_OK;
+    size_t nc = std::max<size_t>(m, std::max<size_t>(1024, cap * 2));
+    T* q = nullptr;
+    if (cudaMallocAsync((void**)&q, nc * sizeof(T), st) != cudaSuccess) return DC_E_NOMEM;
+    if (keep && p) DC_CUDA(cudaMemcpyAsync(q, p, keep * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    if (p) DC_CUDA(cudaFreeAsync(p, st));
+    p = q;
+    cap = nc;
+    return DC_OK;
+  }
+  void release(cudaStream_t st) {
+    if (p) cudaFreeAsync(p, st);
+    p = nullptr;
+    cap = 0;
+  }
+};
+
+int pick_block(int k) {
+  if (const char* env = std::getenv("DCSCHED_BLOCK")) {
+    int b = std::atoi(env);
+    const int H = k * k * k / 4;
+    if (max_hosts_per_thread(b) > 0 && H <= b * max_hosts_per_thread(b)) return b;
+  }
+  if (k <= 4) return 128;
+  if (k <= 8) return 256;
+  if (k <= 16) return 1024;
+  if (k <= 24) return 512;
+  return 512;
+}
+
+size_t g_smem_max = 0;
+bool g_configured = false;
+
+int ensure_configured() {
+  if (g_configured) return DC_OK;
+  int dev = 0;
+  DC_CUDA(cudaGetDevice(&dev));
+  int optin = 0;
+  DC_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  g_smem_max = (size_t)optin;
+  DC_TRY(configure_kernels(g_smem_max));
+  g_configured = true;
+  return DC_OK;
+}
+
+}  // namespace
+
+struct dc_t {
+  dc_config cfg{};
+  int32_t k = 0, half = 0, H = 0, E = 0;
+  cudaStream_t stream = nullptr;
+  int block = 0;
+  size_t smem = 0;
+  // device state: cpu[H], mem[H], ctr[H], pre[H], res[3H]; and the dc_create copy
+  int32_t* d_state = nullptr;
+  int32_t* d_init = nullptr;
+  double* d_W = nullptr;
+  double* d_L1 = nullptr;
+  int32_t* d_err = nullptr;
+  // host request store (pinned): per-container and per-link records in pod
+  // order and the per-pod ranges (see ReqRec)
+  PinnedVec<int4> c_lay, e_lay;
+  PinnedVec<int32_t> p_coff, p_eoff;
+  PinnedVec<ReqRec> reqs;
+  int64_t tot_c = 0, tot_e = 0, tot_p = 0, tot_l = 0;
+  int32_t max_links = 0, max_pods = 0;
+  // device request store
+  DevVec<int4> d_c_lay, d_e_lay;
+  DevVec<int32_t> d_p_coff, d_p_eoff;
+  DevVec<ReqRec> d_reqs;
+  size_t staged = 0;  // requests whose inputs are on the device
+  int64_t st_c = 0, st_e = 0, st_l = 0;
+  // device outputs and their pinned host mirror
+  DevVec<int32_t> o_host, o_cpu, o_mem, o_bw, o_path, o_status, o_ndec;
+  DevVec<double> o_score;
+  PinnedVec<int32_t> m_host, m_cpu, m_mem, m_bw, m_path, m_status, m_ndec;
+  PinnedVec<double> m_score;
+  DevVec<int4> d_scr_pe;
+  DevVec<PodLog> d_scr_log;
+  int32_t scr_links = 0, scr_pods = 0;
+  // operations (FCFS) and their progress
+  std::vector<int32_t> ops;
+  size_t ops_claimed = 0;  // ops taken by a launch
+  std::vector<int64_t> launch_of;   // per request: id of the launch that schedules it
+  std::vector<uint8_t> release_queued;
+  int64_t next_launch = 1;
+  int64_t collected_launch = 0;  // every launch <= this has results in the mirror
+  std::vector<std::pair<int64_t, cudaEvent_t>> inflight;  // async launches
+  uint64_t gen = 0;  // bumped by submit / reset: plans built earlier are stale
+};
+
+struct dc_plan {
+  std::vector<dc_t*> dcs;
+  std::vector<uint64_t> gens;
+  int flags = 0;
+  struct Group {
+    int block;
+    size_t smem;
+    int first, n;
+  };
+  std::vector<Group> groups;
+  std::vector<InstDev> h_desc;  // launch order
+  std::vector<int> inst_of;     // descriptor -> index into dcs
+  InstDev* d_desc = nullptr;
+  int32_t* d_ops = nullptr;
+  unsigned long long* d_counters = nullptr;
+  unsigned long long h_counters[2] = {0, 0};
+  std::vector<cudaStream_t> side;
+  std::vector<cudaEvent_t> fork_ev, join_ev;
+  cudaEvent_t done_ev = nullptr;
+  cudaStream_t home = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  int64_t launch_id = 0;
+  std::vector<size_t> req_begin, req_end;  // per dc: requests scheduled by this plan
+  bool launched = false;
+};
+
+namespace {
+
+int validate_config(const dc_config* c) {
+  if (!c) return DC_E_INVAL;
+  if (c->k < 2 || (c->k & 1) || c->k > kMaxK) return DC_E_INVAL;
+  if (c->host_cpu < 0 || c->host_cpu > 65535 || c->host_mem < 0 || c->host_mem > 65535)
+    return DC_E_INVAL;
+  if (c->link_mbps < 0 || c->link_mbps > (1 << 21) - 1) return DC_E_INVAL;
+  if (c->n_criteria != 4 && c->n_criteria != 6) return DC_E_INVAL;
+  if (c->method != DC_TOPSIS && c->method != DC_AHP) return DC_E_INVAL;
+  if (c->pair_rule != DC_PAIR_RATIO && c->pair_rule != DC_PAIR_DIFF) return DC_E_INVAL;
+  if (c->method == DC_AHP && c->pair_rule == DC_PAIR_DIFF) return DC_E_INVAL;  // not built yet
+  double s = 0.0;
+  for (int v = 0; v < c->n_criteria; ++v) {
+    if (!(c->weights[v] >= 0.0) || !std::isfinite(c->weights[v])) return DC_E_INVAL;
+    s += c->weights[v];
+  }
+  if (!(s > 0.0)) return DC_E_INVAL;
+  return DC_OK;
+}
+
+void settle(dc_t* d, bool wait) {
+  // retire finished async launches
+  auto it = d->inflight.begin();
+  while (it != d->inflight.end()) {
+    cudaError_t e = wait ? cudaEventSynchronize(it->second) : cudaEventQuery(it->second);
+    if (e == cudaSuccess) {
+      d->collected_launch = std::max(d->collected_launch, it->first);
+      cudaEventDestroy(it->second);
+      it = d->inflight.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
+
+// Appends one validated request and its per-pod layout: containers grouped
+// by pod and links grouped by the later of their two pods (index order inside
+// a group), as the records the kernels read.
+int store_request(dc_t* d, const dc_request* q) {
+  const int32_t n = q->n_containers, m = q->n_edges;
+  if (n < 0 || m < 0 || m > kMaxLinksPerRequest) return DC_E_INVAL;
+  if ((n > 0 && (!q->cpu_min || !q->cpu_max || !q->mem_min || !q->mem_max || !q->pod)) ||
+      (m > 0 && (!q->src || !q->dst || !q->bw_min || !q->bw_max)))
+    return DC_E_INVAL;
+  int32_t P = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    if (q->pod[i] < 0 || q->pod[i] >= n) return DC_E_INVAL;
+    if (q->cpu_min[i] < 0 || q->cpu_min[i] > q->cpu_max[i] || q->cpu_max[i] > 65535) return DC_E_INVAL;
+    if (q->mem_min[i] < 0 || q->mem_min[i] > q->mem_max[i] || q->mem_max[i] > 65535) return DC_E_INVAL;
+    P = std::max(P, q->pod[i] + 1);
+  }
+  std::vector<int32_t> pc(P + 1, 0), pe(P + 1, 0);
+  for (int32_t i = 0; i < n; ++i) pc[q->pod[i] + 1] += 1;
+  for (int32_t g = 0; g < P; ++g)
+    if (pc[g + 1] == 0) return DC_E_INVAL;  // pod ids must be dense
+  for (int32_t e = 0; e < m; ++e) {
+    if (q->src[e] < 0 || q->src[e] >= n || q->dst[e] < 0 || q->dst[e] >= n) return DC_E_INVAL;
+    if (q->src[e] == q->dst[e]) return DC_E_INVAL;
+    if (q->bw_min[e] < 0 || q->bw_min[e] > q->bw_max[e]) return DC_E_INVAL;
+    pe[std::max(q->pod[q->src[e]], q->pod[q->dst[e]]) + 1] += 1;
+  }
+  for (int32_t g = 0; g < P; ++g) {
+    pc[g + 1] += pc[g];
+    pe[g + 1] += pe[g];
+  }
+  std::vector<int4> cl(n), el(m);
+  std::vector<int32_t> fillc(pc.begin(), pc.end() - 1), fille(pe.begin(), pe.end() - 1);
+  for (int32_t i = 0; i < n; ++i)
+    cl[fillc[q->pod[i]]++] = make_int4(i, q->cpu_min[i] | (q->cpu_max[i] << 16),
+                                       q->mem_min[i] | (q->mem_max[i] << 16), 0);
+  for (int32_t e = 0; e < m; ++e) {
+    const int32_t ps = q->pod[q->src[e]], pt = q->pod[q->dst[e]];
+    int32_t w = e, other;
+    if (ps == pt) {
+      w |= kLinkIntra;
+      other = q->dst[e];
+    } else if (ps > pt) {  // the later pod holds src
+      w |= kLinkMineSrc;
+      other = q->dst[e];
+    } else {
+      other = q->src[e];
+    }
+    el[fille[std::max(ps, pt)]++] = make_int4(w, other, q->bw_min[e], q->bw_max[e]);
+  }
+  DC_TRY(d->c_lay.append(cl.data(), n));
+  DC_TRY(d->e_lay.append(el.data(), m));
+  DC_TRY(d->p_coff.append(pc.data(), P + 1));
+  DC_TRY(d->p_eoff.append(pe.data(), P + 1));
+  ReqRec r{};
+  r.c_off = d->tot_c;
+  r.e_off = d->tot_e;
+  r.p_off = d->tot_p;
+  r.l_off = d->tot_l;
+  r.n_c = n;
+  r.n_e = m;
+  r.n_p = P;
+  DC_TRY(d->reqs.append(&r, 1));
+  d->tot_c += n;
+  d->tot_e += m;
+  d->tot_p += P;
+  d->tot_l += P + 1;
+  d->max_links = std::max(d->max_links, m);
+  d->max_pods = std::max(d->max_pods, P);
+  return DC_OK;
+}
+
+// Mirrors not-yet-staged requests to the device and sizes outputs/scratch.
+int stage(dc_t* d) {
+  cudaStream_t st = d->stream;
+  settle(d, true);  // no copy into the host mirrors may be in flight below
+  const size_t R = d->reqs.n;
+  DC_TRY(d->d_c_lay.ensure(d->tot_c, d->st_c, st));
+  DC_TRY(d->d_e_lay.ensure(d->tot_e, d->st_e, st));
+  DC_TRY(d->d_p_coff.ensure(d->tot_l, d->st_l, st));
+  DC_TRY(d->d_p_eoff.ensure(d->tot_l, d->st_l, st));
+  DC_TRY(d->d_reqs.ensure(R, d->staged, st));
+  // outputs keep everything already computed
+  const int64_t done_c = d->staged ? d->reqs.p[d->staged - 1].c_off + d->reqs.p[d->staged - 1].n_c : 0;
+  const int64_t done_e = d->staged ? d->reqs.p[d->staged - 1].e_off + d->reqs.p[d->staged - 1].n_e : 0;
+  const int64_t done_p = d->staged ? d->reqs.p[d->staged - 1].p_off + d->reqs.p[d->staged - 1].n_p : 0;
+  DC_TRY(d->o_host.ensure(d->tot_c, done_c, st));
+  DC_TRY(d->o_cpu.ensure(d->tot_c, done_c, st));
+  DC_TRY(d->o_mem.ensure(d->tot_c, done_c, st));
+  DC_TRY(d->o_bw.ensure(d->tot_e, done_e, st));
+  DC_TRY(d->o_path.ensure(6 * d->tot_e, 6 * done_e, st));
+  DC_TRY(d->o_score.ensure(d->tot_p, done_p, st));
+  DC_TRY(d->o_status.ensure(R, d->staged, st));
+  DC_TRY(d->o_ndec.ensure(R, d->staged, st));
+  if (d->max_links > d->scr_links || !d->d_scr_pe.p) {
+    DC_TRY(d->d_scr_pe.ensure(std::max<size_t>(1, d->max_links), 0, st));
+    d->scr_links = (int32_t)d->d_scr_pe.cap;
+  }
+  if (d->max_pods > d->scr_pods || !d->d_scr_log.p) {
+    DC_TRY(d->d_scr_log.ensure(std::max<size_t>(1, d->max_pods), 0, st));
+    d->scr_pods = (int32_t)d->d_scr_log.cap;
+  }
+  if (R > d->staged) {
+    const int64_t c0 = d->st_c, e0 = d->st_e, l0 = d->st_l;
+    const int64_t nc = d->tot_c - c0, ne = d->tot_e - e0, nl = d->tot_l - l0;
+    if (nc) DC_CUDA(cudaMemcpyAsync(d->d_c_lay.p + c0, d->c_lay.p + c0, nc * sizeof(int4), cudaMemcpyHostToDevice, st));
+    if (ne) DC_CUDA(cudaMemcpyAsync(d->d_e_lay.p + e0, d->e_lay.p + e0, ne * sizeof(int4), cudaMemcpyHostToDevice, st));
+    if (nl) {
+      DC_CUDA(cudaMemcpyAsync(d->d_p_coff.p + l0, d->p_coff.p + l0, nl * 4, cudaMemcpyHostToDevice, st));
+      DC_CUDA(cudaMemcpyAsync(d->d_p_eoff.p + l0, d->p_eoff.p + l0, nl * 4, cudaMemcpyHostToDevice, st));
+    }
+    DC_CUDA(cudaMemcpyAsync(d->d_reqs.p + d->staged, d->reqs.p + d->staged,
+                            (R - d->staged) * sizeof(ReqRec), cudaMemcpyHostToDevice, st));
+    d->staged = R;
+    d->st_c = d->tot_c;
+    d->st_e = d->tot_e;
+    d->st_l = d->tot_l;
+  }
+  DC_TRY(d->m_host.resize(d->tot_c));
+  DC_TRY(d->m_cpu.resize(d->tot_c));
+  DC_TRY(d->m_mem.resize(d->tot_c));
+  DC_TRY(d->m_bw.resize(d->tot_e));
+  DC_TRY(d->m_path.resize(6 * d->tot_e));
+  DC_TRY(d->m_score.resize(d->tot_p));
+  DC_TRY(d->m_status.resize(R));
+  DC_TRY(d->m_ndec.resize(R));
+  return DC_OK;
+}
+
+InstDev make_desc(dc_t* d, const int32_t* d_ops, int n_ops, unsigned long long* counters) {
+  InstDev I{};
+  I.k = d->k; I.half = d->half; I.H = d->H; I.E = d->E;
+  I.C = d->cfg.n_criteria; I.method = d->cfg.method; I.rule = d->cfg.pair_rule;
+  I.host_cpu = d->cfg.host_cpu; I.host_mem = d->cfg.host_mem; I.link_mbps = d->cfg.link_mbps;
+  for (int v = 0; v < kMaxC; ++v) I.W[v] = v < I.C ? d->cfg.weights[v] : 0.0;
+  I.L1 = d->d_L1;
+  I.cpu = d->d_state;
+  I.mem = d->d_state + d->H;
+  I.ctr = d->d_state + 2 * d->H;
+  I.pre = d->d_state + 3 * d->H;
+  I.res = d->d_state + 4 * d->H;
+  I.reqs = d->d_reqs.p;
+  I.c_lay = d->d_c_lay.p;
+  I.e_lay = d->d_e_lay.p;
+  I.p_coff = d->d_p_coff.p; I.p_eoff = d->d_p_eoff.p;
+  I.o_host = d->o_host.p; I.o_cpu = d->o_cpu.p; I.o_mem = d->o_mem.p;
+  I.o_bw = d->o_bw.p; I.o_path = d->o_path.p; I.o_status = d->o_status.p; I.o_ndec = d->o_ndec.p;
+  I.o_score = d->o_score.p;
+  I.ops = d_ops;
+  I.n_ops = n_ops;
+  I.scr_links = d->scr_links;
+  I.scr_pods = d->scr_pods;
+  I.scr_pe = d->d_scr_pe.p;
+  I.scr_log = d->d_scr_log.p;
+  I.err = d->d_err;
+  I.counters = counters;
+  return I;
+}
+
+// Enqueues the device work of a plan on stream `st` (used directly and
+// under graph capture).
+int enqueue_plan(dc_plan* p, cudaStream_t st) {
+  if (p->flags & DC_PLAN_RESET)
+    for (dc_t* d : p->dcs)
+      DC_CUDA(cudaMemcpyAsync(d->d_state, d->d_init, sizeof(int32_t) * 7 * (size_t)d->H,
+                              cudaMemcpyDeviceToDevice, st));
+  DC_CUDA(cudaMemsetAsync(p->d_counters, 0, 2 * sizeof(unsigned long long), st));
+  const size_t G = p->groups.size();
+  if (G == 1) {
+    const auto& g = p->groups[0];
+    return launch_schedule(g.block, p->d_desc + g.first, g.n, g.smem, st);
+  }
+  for (size_t i = 0; i < G; ++i) {
+    DC_CUDA(cudaEventRecord(p->fork_ev[i], st));
+    DC_CUDA(cudaStreamWaitEvent(p->side[i], p->fork_ev[i], 0));
+    const auto& g = p->groups[i];
+    DC_TRY(launch_schedule(g.block, p->d_desc + g.first, g.n, g.smem, p->side[i]));
+    DC_CUDA(cudaEventRecord(p->join_ev[i], p->side[i]));
+  }
+  for (size_t i = 0; i < G; ++i) DC_CUDA(cudaStreamWaitEvent(st, p->join_ev[i], 0));
+  return DC_OK;
+}
+
+// Releases a plan's resources; device buffers are freed in stream order on
+// the plan's home stream, so work already enqueued may still be running.
+void destroy_plan_resources(dc_plan* p) {
+  for (auto s : p->side) cudaStreamDestroy(s);
+  for (auto e : p->fork_ev) cudaEventDestroy(e);
+  for (auto e : p->join_ev) cudaEventDestroy(e);
+  if (p->done_ev) cudaEventDestroy(p->done_ev);
+  if (p->exec) cudaGraphExecDestroy(p->exec);
+  if (p->graph) cudaGraphDestroy(p->graph);
+  if (p->d_desc) cudaFreeAsync(p->d_desc, p->home);
+  if (p->d_ops) cudaFreeAsync(p->d_ops, p->home);
+  if (p->d_counters) cudaFreeAsync(p->d_counters, p->home);
+}
+
+// D2H of a plan's results into the instances' pinned mirrors (stream-ordered).
+int enqueue_collect(dc_plan* p, cudaStream_t st) {
+  for (size_t i = 0; i < p->dcs.size(); ++i) {
+    dc_t* d = p->dcs[i];
+    const size_t r0 = p->req_begin[i], r1 = p->req_end[i];
+    if (d->reqs.n == 0) continue;
+    // status of every request (releases change earlier ones)
+    DC_CUDA(cudaMemcpyAsync(d->m_status.p, d->o_status.p, d->reqs.n * 4, cudaMemcpyDeviceToHost, st));
+    if (r1 <= r0) continue;
+    const ReqRec a = d->reqs.p[r0], b = d->reqs.p[r1 - 1];
+    const int64_t c0 = a.c_off, c1 = b.c_off + b.n_c, e0 = a.e_off, e1 = b.e_off + b.n_e;
+    const int64_t p0 = a.p_off, p1 = b.p_off + b.n_p;
+    if (c1 > c0) {
+      DC_CUDA(cudaMemcpyAsync(d->m_host.p + c0, d->o_host.p + c0, (c1 - c0) * 4, cudaMemcpyDeviceToHost, st));
+      DC_CUDA(cudaMemcpyAsync(d->m_cpu.p + c0, d->o_cpu.p + c0, (c1 - c0) * 4, cudaMemcpyDeviceToHost, st));
+      DC_CUDA(cudaMemcpyAsync(d->m_mem.p + c0, d->o_mem.p + c0, (c1 - c0) * 4, cudaMemcpyDeviceToHost, st));
+    }
+    if (e1 > e0) {
+      DC_CUDA(cudaMemcpyAsync(d->m_bw.p + e0, d->o_bw.p + e0, (e1 - e0) * 4, cudaMemcpyDeviceToHost, st));
+      DC_CUDA(cudaMemcpyAsync(d->m_path.p + 6 * e0, d->o_path.p + 6 * e0, (e1 - e0) * 24, cudaMemcpyDeviceToHost, st));
+    }
+    if (p1 > p0)
+      DC_CUDA(cudaMemcpyAsync(d->m_score.p + p0, d->o_score.p + p0, (p1 - p0) * 8, cudaMemcpyDeviceToHost, st));
+    DC_CUDA(cudaMemcpyAsync(d->m_ndec.p + r0, d->o_ndec.p + r0, (r1 - r0) * 4, cudaMemcpyDeviceToHost, st));
+  }
+  return DC_OK;
+}
+
+int check_stale(const dc_plan* p) {
+  for (size_t i = 0; i < p->dcs.size(); ++i)
+    if (p->dcs[i]->gen != p->gens[i]) return DC_E_BUSY;
+  return DC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* dc_strerror(int code) {
+  switch (code) {
+    case DC_OK: return "ok";
+    case DC_E_INVAL: return "invalid argument or request";
+    case DC_E_NOMEM: return "out of memory";
+    case DC_E_CUDA: return "CUDA error";
+    case DC_E_TIMEOUT: return "device wait timed out";
+    case DC_E_NOTFOUND: return "unknown request id";
+    case DC_E_BUSY: return "state does not allow the call";
+    default: return "unknown error";
+  }
+}
+
+int dc_create(const dc_config* cfg, void* cuda_stream, dc_t** out) {
+  if (!out) return DC_E_INVAL;
+  *out = nullptr;
+  DC_TRY(validate_config(cfg));
+  DC_TRY(ensure_configured());
+  dc_t* d = new (std::nothrow) dc_t();
+  if (!d) return DC_E_NOMEM;
+  d->cfg = *cfg;
+  d->cfg.pre_cpu = d->cfg.pre_mem = d->cfg.pre_link = nullptr;
+  d->k = cfg->k;
+  d->half = cfg->k / 2;
+  d->H = cfg->k * cfg->k * cfg->k / 4;
+  d->E = cfg->k * cfg->k / 2;
+  d->stream = (cudaStream_t)cuda_stream;
+  d->block = pick_block(d->k);
+  d->smem = smem_layout(d->k, d->block, ctx_bytes()).total;
+  if (d->smem > g_smem_max || d->H > d->block * max_hosts_per_thread(d->block)) {
+    delete d;
+    return DC_E_INVAL;
+  }
+  const int H = d->H;
+  std::vector<int32_t> st(7 * (size_t)H);
+  for (int h = 0; h < H; ++h) {
+    const int uc = cfg->pre_cpu ? cfg->pre_cpu[h] : 0, um = cfg->pre_mem ? cfg->pre_mem[h] : 0;
+    if (uc < 0 || uc > cfg->host_cpu || um < 0 || um > cfg->host_mem) {
+      delete d;
+      return DC_E_INVAL;
+    }
+    st[h] = cfg->host_cpu - uc;
+    st[H + h] = cfg->host_mem - um;
+    st[2 * H + h] = 0;
+    st[3 * H + h] = (uc > 0 || um > 0) ? 1 : 0;
+  }
+  for (int l = 0; l < 3 * H; ++l) {
+    const int ul = cfg->pre_link ? cfg->pre_link[l] : 0;
+    if (ul < 0 || ul > cfg->link_mbps) {
+      delete d;
+      return DC_E_INVAL;
+    }
+    st[4 * H + l] = cfg->link_mbps - ul;
+  }
+  int rc = DC_OK;
+  if (cudaMalloc((void**)&d->d_state, st.size() * 4) != cudaSuccess ||
+      cudaMalloc((void**)&d->d_init, st.size() * 4) != cudaSuccess ||
+      cudaMalloc((void**)&d->d_W, kMaxC * sizeof(double)) != cudaSuccess ||
+      cudaMalloc((void**)&d->d_L1, kMaxC * sizeof(double)) != cudaSuccess ||
+      cudaMalloc((void**)&d->d_err, sizeof(int32_t)) != cudaSuccess)
+    rc = DC_E_NOMEM;
+  if (rc == DC_OK) {
+    double W[kMaxC] = {0};
+    for (int v = 0; v < cfg->n_criteria; ++v) W[v] = cfg->weights[v];
+    if (cudaMemcpy(d->d_init, st.data(), st.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d->d_state, st.data(), st.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d->d_W, W, sizeof(W), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(d->d_err, 0, sizeof(int32_t)) != cudaSuccess)
+      rc = DC_E_CUDA;
+  }
+  if (rc == DC_OK) rc = launch_weights(cfg->n_criteria, cfg->pair_rule, d->d_W, d->d_L1, d->stream);
+  if (rc == DC_OK) rc = cuda_rc(cudaStreamSynchronize(d->stream));
+  if (rc != DC_OK) {
+    dc_destroy(d);
+    return rc;
+  }
+  *out = d;
+  return DC_OK;
+}
+
+void dc_destroy(dc_t* d) {
+  if (!d) return;
+  cudaStreamSynchronize(d->stream);
+  settle(d, true);
+  cudaStream_t st = d->stream;
+  d->d_c_lay.release(st); d->d_e_lay.release(st); d->d_p_coff.release(st); d->d_p_eoff.release(st);
+  d->d_reqs.release(st);
+  d->o_host.release(st); d->o_cpu.release(st); d->o_mem.release(st); d->o_bw.release(st);
+  d->o_path.release(st); d->o_status.release(st); d->o_ndec.release(st); d->o_score.release(st);
+  d->d_scr_pe.release(st);
+  d->d_scr_log.release(st);
+  cudaStreamSynchronize(st);
+  d->c_lay.release(); d->e_lay.release(); d->p_coff.release(); d->p_eoff.release();
+  d->reqs.release();
+  d->m_host.release(); d->m_cpu.release(); d->m_mem.release(); d->m_bw.release();
+  d->m_path.release(); d->m_status.release(); d->m_ndec.release(); d->m_score.release();
+  if (d->d_state) cudaFree(d->d_state);
+  if (d->d_init) cudaFree(d->d_init);
+  if (d->d_W) cudaFree(d->d_W);
+  if (d->d_L1) cudaFree(d->d_L1);
+  if (d->d_err) cudaFree(d->d_err);
+  delete d;
+}
+
+int dc_submit_request(dc_t* d, const dc_request* q, int64_t* req_id) {
+  if (!d || !q) return DC_E_INVAL;
+  const size_t r = d->reqs.n;
+  if (r >= (size_t)(kOpRelease - 1)) return DC_E_INVAL;
+  DC_TRY(store_request(d, q));
+  d->ops.push_back((int32_t)r);
+  d->launch_of.push_back(0);
+  d->release_queued.push_back(0);
+  d->gen += 1;
+  if (req_id) *req_id = (int64_t)r;
+  return DC_OK;
+}
+
+int dc_release(dc_t* d, int64_t req_id) {
+  if (!d) return DC_E_INVAL;
+  if (req_id < 0 || (size_t)req_id >= d->reqs.n) return DC_E_NOTFOUND;
+  if (d->release_queued[req_id]) return DC_E_BUSY;
+  d->release_queued[req_id] = 1;
+  d->ops.push_back((int32_t)req_id | kOpRelease);
+  d->gen += 1;
+  return DC_OK;
+}
+
+int dc_plan_create(dc_t* const* dcs, int32_t n, int32_t flags, dc_plan** out) {
+  if (!dcs || n <= 0 || !out) return DC_E_INVAL;
+  *out = nullptr;
+  for (int32_t i = 0; i < n; ++i) {
+    if (!dcs[i]) return DC_E_INVAL;
+    for (int32_t j = 0; j < i; ++j)
+      if (dcs[j] == dcs[i]) return DC_E_INVAL;
+  }
+  dc_plan* p = new (std::nothrow) dc_plan();
+  if (!p) return DC_E_NOMEM;
+  p->flags = flags;
+  p->home = dcs[0]->stream;
+  int rc = DC_OK;
+  // ops of this plan, per instance
+  std::vector<size_t> op0(n), op1(n);
+  std::vector<int32_t> all_ops;
+  for (int32_t i = 0; i < n && rc == DC_OK; ++i) {
+    dc_t* d = dcs[i];
+    rc = stage(d);
+    if (rc != DC_OK) break;
+    op0[i] = (flags & DC_PLAN_RESET) ? 0 : d->ops_claimed;
+    op1[i] = d->ops.size();
+    all_ops.insert(all_ops.end(), d->ops.begin() + op0[i], d->ops.begin() + op1[i]);
+  }
+  if (rc == DC_OK) {
+    p->dcs.assign(dcs, dcs + n);
+    // launch order: groups of equal k, largest first; inside a group by work
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::vector<double> work(n, 0.0);
+    for (int i = 0; i < n; ++i) {
+      dc_t* d = dcs[i];
+      double c = 0;
+      for (size_t o = op0[i]; o < op1[i]; ++o)
+        if (!(d->ops[o] & kOpRelease)) c += d->reqs.p[d->ops[o]].n_p;
+      work[i] = c * d->H;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+      if (dcs[a]->k != dcs[b]->k) return dcs[a]->k > dcs[b]->k;
+      return work[a] > work[b];
+    });
+    std::vector<size_t> op_base(n);
+    size_t acc = 0;
+    for (int i = 0; i < n; ++i) {
+      op_base[i] = acc;
+      acc += op1[i] - op0[i];
+    }
+    const size_t n_ops_total = std::max<size_t>(1, all_ops.size());
+    if (cudaMallocAsync((void**)&p->d_ops, n_ops_total * 4, p->home) != cudaSuccess ||
+        cudaMallocAsync((void**)&p->d_desc, n * sizeof(InstDev), p->home) != cudaSuccess ||
+        cudaMallocAsync((void**)&p->d_counters, 2 * sizeof(unsigned long long), p->home) !=
+            cudaSuccess)
+      rc = DC_E_NOMEM;
+    if (rc == DC_OK && !all_ops.empty())
+      rc = cuda_rc(cudaMemcpyAsync(p->d_ops, all_ops.data(), all_ops.size() * 4,
+                                   cudaMemcpyHostToDevice, p->home));
+    for (int j = 0; j < n && rc == DC_OK; ++j) {
+      const int i = order[j];
+      dc_t* d = dcs[i];
+      p->h_desc.push_back(make_desc(d, p->d_ops + op_base[i], (int)(op1[i] - op0[i]), p->d_counters));
+      p->inst_of.push_back(i);
+      if (p->groups.empty() || dcs[order[p->groups.back().first]]->k != d->k)
+        p->groups.push_back({d->block, d->smem, j, 0});
+      p->groups.back().n += 1;
+    }
+    if (rc == DC_OK)
+      rc = cuda_rc(cudaMemcpyAsync(p->d_desc, p->h_desc.data(), n * sizeof(InstDev),
+                                   cudaMemcpyHostToDevice, p->home));
+    // the home stream must see every instance's staging
+    for (int i = 0; i < n && rc == DC_OK; ++i)
+      if (dcs[i]->stream != p->home) rc = cuda_rc(cudaStreamSynchronize(dcs[i]->stream));
+    if (rc == DC_OK) rc = cuda_rc(cudaStreamSynchronize(p->home));
+    const size_t G = p->groups.size();
+    for (size_t gi = 0; gi < G && G > 1 && rc == DC_OK; ++gi) {
+      cudaStream_t s;
+      cudaEvent_t a, b;
+      if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&a, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreateWithFlags(&b, cudaEventDisableTiming) != cudaSuccess) {
+        rc = DC_E_CUDA;
+        break;
+      }
+      p->side.push_back(s);
+      p->fork_ev.push_back(a);
+      p->join_ev.push_back(b);
+    }
+    if (rc == DC_OK) rc = cuda_rc(cudaEventCreateWithFlags(&p->done_ev, cudaEventDisableTiming));
+    if (rc == DC_OK && (flags & DC_PLAN_GRAPH)) {
+      cudaStream_t cap;
+      rc = cuda_rc(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+      if (rc == DC_OK) {
+        rc = cuda_rc(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
+        if (rc == DC_OK) {
+          int rc2 = enqueue_plan(p, cap);
+          cudaError_t e = cudaStreamEndCapture(cap, &p->graph);
+          rc = rc2 != DC_OK ? rc2 : cuda_rc(e);
+        }
+        if (rc == DC_OK) rc = cuda_rc(cudaGraphInstantiate(&p->exec, p->graph, 0));
+        cudaStreamDestroy(cap);
+      }
+    }
+  }
+  if (rc != DC_OK) {
+    destroy_plan_resources(p);
+    delete p;
+    return rc;
+  }
+  // claim the ops and record which requests this plan schedules
+  p->launch_id = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    dc_t* d = dcs[i];
+    size_t rb = d->reqs.n, re = 0;
+    for (size_t o = op0[i]; o < op1[i]; ++o)
+      if (!(d->ops[o] & kOpRelease)) {
+        rb = std::min<size_t>(rb, d->ops[o]);
+        re = std::max<size_t>(re, d->ops[o] + 1);
+      }
+    if (re <= rb) rb = re = 0;
+    p->req_begin.push_back(rb);
+    p->req_end.push_back(re);
+    d->ops_claimed = op1[i];
+    p->gens.push_back(d->gen);
+  }
+  *out = p;
+  return DC_OK;
+}
+
+int dc_plan_launch(dc_plan* p, void* cuda_stream) {
+  if (!p) return DC_E_INVAL;
+  DC_TRY(check_stale(p));
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (p->exec) {
+    DC_CUDA(cudaGraphLaunch(p->exec, st));
+  } else {
+    DC_TRY(enqueue_plan(p, st));
+  }
+  DC_CUDA(cudaEventRecord(p->done_ev, st));
+  p->launched = true;
+  return DC_OK;
+}
+
+int dc_plan_collect(dc_plan* p) {
+  if (!p || !p->launched) return DC_E_INVAL;
+  DC_TRY(check_stale(p));
+  DC_CUDA(cudaStreamWaitEvent(p->home, p->done_ev, 0));
+  DC_TRY(enqueue_collect(p, p->home));
+  DC_CUDA(cudaStreamSynchronize(p->home));
+  DC_CUDA(cudaMemcpy(p->h_counters, p->d_counters, 2 * sizeof(unsigned long long),
+                     cudaMemcpyDeviceToHost));
+  int32_t err = 0;
+  for (dc_t* d : p->dcs) {
+    DC_CUDA(cudaMemcpy(&err, d->d_err, sizeof(err), cudaMemcpyDeviceToHost));
+    if (err != 0) return err;
+  }
+  for (size_t i = 0; i < p->dcs.size(); ++i) {
+    dc_t* d = p->dcs[i];
+    const int64_t id = d->next_launch++;
+    for (size_t r = p->req_begin[i]; r < p->req_end[i]; ++r) d->launch_of[r] = id;
+    d->collected_launch = std::max(d->collected_launch, id);
+  }
+  return DC_OK;
+}
+
+int dc_plan_stats(dc_plan* p, int64_t* decisions, int64_t* host_rankings, int32_t* kernels) {
+  if (!p) return DC_E_INVAL;
+  if (decisions) *decisions = (int64_t)p->h_counters[0];
+  if (host_rankings) *host_rankings = (int64_t)p->h_counters[1];
+  if (kernels) *kernels = (int32_t)p->groups.size();
+  return DC_OK;
+}
+
+void dc_plan_destroy(dc_plan* p) {
+  if (!p) return;
+  if (p->launched) cudaEventSynchronize(p->done_ev);
+  destroy_plan_resources(p);
+  cudaStreamSynchronize(p->home);
+  delete p;
+}
+
+int dc_schedule(dc_t* const* dcs, int32_t n, int32_t flags) {
+  if (!dcs || n <= 0) return DC_E_INVAL;
+  dc_plan* p = nullptr;
+  DC_TRY(dc_plan_create(dcs, n, 0, &p));
+  int rc = dc_plan_launch(p, p->home);
+  if (rc == DC_OK) rc = cuda_rc(cudaStreamWaitEvent(p->home, p->done_ev, 0));
+  if (rc == DC_OK) rc = enqueue_collect(p, p->home);
+  if (rc == DC_OK) {
+    for (size_t i = 0; i < p->dcs.size(); ++i) {
+      dc_t* d = p->dcs[i];
+      const int64_t id = d->next_launch++;
+      for (size_t r = p->req_begin[i]; r < p->req_end[i]; ++r) d->launch_of[r] = id;
+      cudaEvent_t ev;
+      if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+        rc = DC_E_CUDA;
+        break;
+      }
+      cudaEventRecord(ev, p->home);
+      d->inflight.push_back({id, ev});
+    }
+  }
+  if (rc == DC_OK && flags == DC_SCHED_SYNC) {
+    rc = cuda_rc(cudaStreamSynchronize(p->home));
+    for (dc_t* d : p->dcs) settle(d, true);
+    int32_t err = 0;
+    for (dc_t* d : p->dcs) {
+      if (rc != DC_OK) break;
+      rc = cuda_rc(cudaMemcpy(&err, d->d_err, sizeof(err), cudaMemcpyDeviceToHost));
+      if (rc == DC_OK && err != 0) rc = err;
+    }
+  }
+  // stream-ordered: the plan's device buffers are released after its work
+  destroy_plan_resources(p);
+  delete p;
+  return rc;
+}
+
+int dc_query(dc_t* d, int64_t req_id, dc_result* out, int32_t wait) {
+  if (!d || !out) return DC_E_INVAL;
+  if (req_id < 0 || (size_t)req_id >= d->reqs.n) return DC_E_NOTFOUND;
+  const int64_t id = d->launch_of[req_id];
+  if (id == 0) {
+    out->status = DC_PENDING;
+    return DC_OK;
+  }
+  if (id > d->collected_launch) {
+    settle(d, wait != 0);
+    if (id > d->collected_launch) {
+      out->status = DC_PENDING;
+      return DC_OK;
+    }
+  }
+  const ReqRec q = d->reqs.p[req_id];
+  out->status = d->m_status.p[req_id] & 0xff;
+  out->n_decisions = d->m_ndec.p[req_id];
+  if (out->host) std::memcpy(out->host, d->m_host.p + q.c_off, q.n_c * 4);
+  if (out->cpu) std::memcpy(out->cpu, d->m_cpu.p + q.c_off, q.n_c * 4);
+  if (out->mem) std::memcpy(out->mem, d->m_mem.p + q.c_off, q.n_c * 4);
+  if (out->bw) std::memcpy(out->bw, d->m_bw.p + q.e_off, q.n_e * 4);
+  if (out->path) std::memcpy(out->path, d->m_path.p + 6 * q.e_off, (size_t)q.n_e * 24);
+  if (out->pod_score) std::memcpy(out->pod_score, d->m_score.p + q.p_off, q.n_p * 8);
+  return DC_OK;
+}
+
+int dc_query_state(dc_t* d, int32_t field, int32_t* out, int64_t len) {
+  if (!d || !out) return DC_E_INVAL;
+  int64_t off, n;
+  switch (field) {
+    case DC_FIELD_FREE_CPU: off = 0; n = d->H; break;
+    case DC_FIELD_FREE_MEM: off = d->H; n = d->H; break;
+    case DC_FIELD_CTR: off = 2 * (int64_t)d->H; n = d->H; break;
+    case DC_FIELD_PRE: off = 3 * (int64_t)d->H; n = d->H; break;
+    case DC_FIELD_LINK_RES: off = 4 * (int64_t)d->H; n = 3 * (int64_t)d->H; break;
+    default: return DC_E_INVAL;
+  }
+  if (len < n) return DC_E_INVAL;
+  DC_CUDA(cudaStreamSynchronize(d->stream));
+  DC_CUDA(cudaMemcpy(out, d->d_state + off, n * 4, cudaMemcpyDeviceToHost));
+  return DC_OK;
+}
+
+int dc_reset(dc_t* d) {
+  if (!d) return DC_E_INVAL;
+  DC_CUDA(cudaStreamSynchronize(d->stream));
+  settle(d, true);
+  DC_CUDA(cudaMemcpy(d->d_state, d->d_init, sizeof(int32_t) * 7 * (size_t)d->H,
+                     cudaMemcpyDeviceToDevice));
+  d->c_lay.n = d->e_lay.n = 0;
+  d->p_coff.n = d->p_eoff.n = 0;
+  d->reqs.n = 0;
+  d->tot_c = d->tot_e = d->tot_p = d->tot_l = 0;
+  d->staged = 0;
+  d->st_c = d->st_e = d->st_l = 0;
+  d->ops.clear();
+  d->ops_claimed = 0;
+  d->launch_of.clear();
+  d->release_queued.clear();
+  d->gen += 1;
+  return DC_OK;
+}
+
+int dc_rank_hosts(dc_t* d, const dc_request* q, int32_t pod, const int32_t* host_of,
+                  int32_t* feasible, float* score32, double* score64, int32_t* crit) {
+  if (!d || !q || !host_of) return DC_E_INVAL;
+  // a temporary instance view holding only this request
+  dc_t tmp;
+  tmp.cfg = d->cfg;
+  tmp.k = d->k; tmp.half = d->half; tmp.H = d->H; tmp.E = d->E;
+  tmp.stream = d->stream;
+  int rc = store_request(&tmp, q);
+  if (rc != DC_OK) return rc;
+  const ReqRec r = tmp.reqs.p[0];
+  if (pod < 0 || pod >= r.n_p) rc = DC_E_INVAL;
+  // containers of earlier pods must be placed
+  for (int32_t i = 0; i < r.n_c && rc == DC_OK; ++i) {
+    const int32_t g = q->pod[i];
+    if (g < pod && (host_of[i] < 0 || host_of[i] >= d->H)) rc = DC_E_INVAL;
+  }
+  cudaStream_t st = d->stream;
+  const int H = d->H, C = d->cfg.n_criteria;
+  int32_t *d_host_of = nullptr, *d_feas = nullptr, *d_crit = nullptr, *d_nv = nullptr;
+  float* d_s32 = nullptr;
+  double* d_s64 = nullptr;
+  InstDev* d_desc = nullptr;
+  if (rc == DC_OK) rc = stage(&tmp);
+  if (rc == DC_OK &&
+      (cudaMalloc((void**)&d_host_of, std::max(1, r.n_c) * 4) != cudaSuccess ||
+       cudaMalloc((void**)&d_feas, H * 4) != cudaSuccess ||
+       cudaMalloc((void**)&d_crit, (size_t)H * C * 4) != cudaSuccess ||
+       cudaMalloc((void**)&d_nv, 4) != cudaSuccess ||
+       cudaMalloc((void**)&d_s32, H * 4) != cudaSuccess ||
+       cudaMalloc((void**)&d_s64, H * 8) != cudaSuccess ||
+       cudaMalloc((void**)&d_desc, sizeof(InstDev)) != cudaSuccess))
+    rc = DC_E_NOMEM;
+  int32_t nviable = 0;
+  if (rc == DC_OK) {
+    tmp.d_state = d->d_state;
+    tmp.d_L1 = d->d_L1;
+    tmp.d_err = d->d_err;
+    InstDev I = make_desc(&tmp, nullptr, 0, nullptr);
+    if (r.n_c) rc = cuda_rc(cudaMemcpyAsync(d_host_of, host_of, r.n_c * 4, cudaMemcpyHostToDevice, st));
+    if (rc == DC_OK) rc = cuda_rc(cudaMemcpyAsync(d_desc, &I, sizeof(I), cudaMemcpyHostToDevice, st));
+    if (rc == DC_OK)
+      rc = launch_rank(d->block, d_desc, 0, pod, d_host_of, d_feas, d_s32, d_s64, d_crit, d_nv,
+                       d->smem, st);
+    if (rc == DC_OK) rc = cuda_rc(cudaStreamSynchronize(st));
+    if (rc == DC_OK && feasible) rc = cuda_rc(cudaMemcpy(feasible, d_feas, H * 4, cudaMemcpyDeviceToHost));
+    if (rc == DC_OK && score32) rc = cuda_rc(cudaMemcpy(score32, d_s32, H * 4, cudaMemcpyDeviceToHost));
+    if (rc == DC_OK && score64) rc = cuda_rc(cudaMemcpy(score64, d_s64, H * 8, cudaMemcpyDeviceToHost));
+    if (rc == DC_OK && crit) rc = cuda_rc(cudaMemcpy(crit, d_crit, (size_t)H * C * 4, cudaMemcpyDeviceToHost));
+    if (rc == DC_OK) rc = cuda_rc(cudaMemcpy(&nviable, d_nv, 4, cudaMemcpyDeviceToHost));
+  }
+  cudaFree(d_host_of); cudaFree(d_feas); cudaFree(d_crit); cudaFree(d_nv);
+  cudaFree(d_s32); cudaFree(d_s64); cudaFree(d_desc);
+  // release the temporary view's buffers (it borrowed state, L1 and err)
+  cudaStreamSynchronize(st);
+  tmp.d_c_lay.release(st); tmp.d_e_lay.release(st); tmp.d_p_coff.release(st); tmp.d_p_eoff.release(st);
+  tmp.d_reqs.release(st);
+  tmp.o_host.release(st); tmp.o_cpu.release(st); tmp.o_mem.release(st); tmp.o_bw.release(st);
+  tmp.o_path.release(st); tmp.o_status.release(st); tmp.o_ndec.release(st); tmp.o_score.release(st);
+  tmp.d_scr_pe.release(st);
+  tmp.d_scr_log.release(st);
+  tmp.c_lay.release(); tmp.e_lay.release(); tmp.p_coff.release(); tmp.p_eoff.release();
+  tmp.reqs.release();
+  tmp.m_host.release(); tmp.m_cpu.release(); tmp.m_mem.release(); tmp.m_bw.release();
+  tmp.m_path.release(); tmp.m_status.release(); tmp.m_ndec.release(); tmp.m_score.release();
+  cudaStreamSynchronize(st);
+  tmp.d_state = nullptr; tmp.d_L1 = nullptr; tmp.d_err = nullptr;
+  return rc == DC_OK ? nviable : rc;
+}
+
+}  // extern "C"

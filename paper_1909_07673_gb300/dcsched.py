@@ -1,0 +1,255 @@
+"""ctypes binding of libdcsched.so (include/dcsched.h).
+
+Argument marshalling only: every step of the scheduling path runs in the CUDA
+library.  Importing this module without the built library raises; there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Dict, Iterable, List, Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdcsched.so")
+
+TOPSIS, AHP = 0, 1
+RATIO, DIFF = 0, 1
+PENDING, ACCEPTED, REJECTED = 0, 1, 2
+SCHED_SYNC, SCHED_ASYNC = 0, 1
+PLAN_GRAPH, PLAN_RESET = 1, 2
+FREE_CPU, FREE_MEM, CTR, PRE, LINK_RES = 0, 1, 2, 3, 4
+
+_i32p = C.POINTER(C.c_int32)
+_i64p = C.POINTER(C.c_int64)
+_f32p = C.POINTER(C.c_float)
+_f64p = C.POINTER(C.c_double)
+
+
+class DcError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__("%s: %s (%d)" % (what, strerror(code), code))
+        self.code = code
+
+
+class _Config(C.Structure):
+    _fields_ = [("k", C.c_int32), ("host_cpu", C.c_int32), ("host_mem", C.c_int32),
+                ("link_mbps", C.c_int32), ("n_criteria", C.c_int32), ("method", C.c_int32),
+                ("pair_rule", C.c_int32), ("weights", C.c_double * 6),
+                ("pre_cpu", _i32p), ("pre_mem", _i32p), ("pre_link", _i32p)]
+
+
+class _Request(C.Structure):
+    _fields_ = [("n_containers", C.c_int32), ("n_edges", C.c_int32),
+                ("cpu_min", _i32p), ("cpu_max", _i32p), ("mem_min", _i32p), ("mem_max", _i32p),
+                ("pod", _i32p), ("src", _i32p), ("dst", _i32p), ("bw_min", _i32p),
+                ("bw_max", _i32p)]
+
+
+class _Result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("n_decisions", C.c_int32), ("host", _i32p),
+                ("cpu", _i32p), ("mem", _i32p), ("bw", _i32p), ("path", _i32p),
+                ("pod_score", _f64p)]
+
+
+_lib = None
+
+
+def lib():
+    """Loads libdcsched.so; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libdcsched.so not built: run __graft_entry__.build() "
+                              "(or python -m paper_1909_07673_gb300.build)")
+        L = C.CDLL(LIB_PATH)
+        L.dc_strerror.restype = C.c_char_p
+        L.dc_strerror.argtypes = [C.c_int]
+        L.dc_create.argtypes = [C.POINTER(_Config), C.c_void_p, C.POINTER(C.c_void_p)]
+        L.dc_destroy.argtypes = [C.c_void_p]
+        L.dc_destroy.restype = None
+        L.dc_submit_request.argtypes = [C.c_void_p, C.POINTER(_Request), _i64p]
+        L.dc_release.argtypes = [C.c_void_p, C.c_int64]
+        L.dc_schedule.argtypes = [C.POINTER(C.c_void_p), C.c_int32, C.c_int32]
+        L.dc_query.argtypes = [C.c_void_p, C.c_int64, C.POINTER(_Result), C.c_int32]
+        L.dc_query_state.argtypes = [C.c_void_p, C.c_int32, _i32p, C.c_int64]
+        L.dc_rank_hosts.argtypes = [C.c_void_p, C.POINTER(_Request), C.c_int32, _i32p, _i32p,
+                                    _f32p, _f64p, _i32p]
+        L.dc_reset.argtypes = [C.c_void_p]
+        L.dc_plan_create.argtypes = [C.POINTER(C.c_void_p), C.c_int32, C.c_int32,
+                                     C.POINTER(C.c_void_p)]
+        L.dc_plan_launch.argtypes = [C.c_void_p, C.c_void_p]
+        L.dc_plan_collect.argtypes = [C.c_void_p]
+        L.dc_plan_stats.argtypes = [C.c_void_p, _i64p, _i64p, _i32p]
+        L.dc_plan_destroy.argtypes = [C.c_void_p]
+        L.dc_plan_destroy.restype = None
+        _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return lib().dc_strerror(code).decode()
+
+
+def _check(rc: int, what: str) -> int:
+    if rc < 0:
+        raise DcError(rc, what)
+    return rc
+
+
+def _p(a: np.ndarray, t):
+    return a.ctypes.data_as(t)
+
+
+def _stream_handle(stream) -> Optional[int]:
+    """Accepts None, an int handle or an object with .cuda_stream (torch)."""
+    if stream is None:
+        return None
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+class _Req:
+    def __init__(self, q: Dict[str, np.ndarray]):
+        self.a = {k: np.ascontiguousarray(q[k], np.int32) for k in (
+            "cpu_min", "cpu_max", "mem_min", "mem_max", "pod", "src", "dst", "bw_min", "bw_max")}
+        a = self.a
+        self.s = _Request(len(a["pod"]), len(a["src"]), *(_p(a[n], _i32p) for n in (
+            "cpu_min", "cpu_max", "mem_min", "mem_max", "pod", "src", "dst", "bw_min", "bw_max")))
+        self.n_pods = int(a["pod"].max()) + 1 if len(a["pod"]) else 0
+
+
+class DataCenter:
+    """One resident data center (dc_t)."""
+
+    def __init__(self, k, host_cpu, host_mem, link_mbps, n_criteria, method, pair_rule, weights,
+                 pre_cpu=None, pre_mem=None, pre_link=None, stream=None):
+        w = (C.c_double * 6)(*([float(x) for x in weights] + [0.0] * (6 - len(weights))))
+        keep = [None if a is None else np.ascontiguousarray(a, np.int32)
+                for a in (pre_cpu, pre_mem, pre_link)]
+        cfg = _Config(k, host_cpu, host_mem, link_mbps, n_criteria, method, pair_rule, w,
+                      *(None if a is None else _p(a, _i32p) for a in keep))
+        h = C.c_void_p()
+        _check(lib().dc_create(C.byref(cfg), _stream_handle(stream), C.byref(h)), "dc_create")
+        self.h = h
+        self.k = k
+        self.H = k ** 3 // 4
+        self.n_criteria = n_criteria
+        self._reqs: List[_Req] = []
+
+    @classmethod
+    def from_instance(cls, inst, stream=None) -> "DataCenter":
+        return cls(inst.k, inst.host_cpu, inst.host_mem, inst.link_mbps, inst.n_criteria,
+                   inst.method, inst.pair_rule, inst.weights, inst.pre_cpu, inst.pre_mem,
+                   inst.pre_link, stream=stream)
+
+    def close(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.dc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def submit(self, q: Dict[str, np.ndarray]) -> int:
+        r = _Req(q)
+        rid = C.c_int64()
+        _check(lib().dc_submit_request(self.h, C.byref(r.s), C.byref(rid)), "dc_submit_request")
+        self._reqs.append(r)
+        return rid.value
+
+    def release(self, req_id: int) -> None:
+        _check(lib().dc_release(self.h, req_id), "dc_release")
+
+    def query(self, req_id: int, wait: bool = True) -> Dict[str, np.ndarray]:
+        r = self._reqs[req_id]
+        n, m, P = len(r.a["pod"]), len(r.a["src"]), r.n_pods
+        out = {"host": np.zeros(n, np.int32), "cpu": np.zeros(n, np.int32),
+               "mem": np.zeros(n, np.int32), "bw": np.zeros(m, np.int32),
+               "path": np.zeros(6 * m, np.int32), "pod_score": np.zeros(P, np.float64)}
+        res = _Result(0, 0, *(_p(out[x], _i32p) for x in ("host", "cpu", "mem", "bw", "path")),
+                      _p(out["pod_score"], _f64p))
+        _check(lib().dc_query(self.h, req_id, C.byref(res), 1 if wait else 0), "dc_query")
+        out["status"] = int(res.status)
+        out["n_decisions"] = int(res.n_decisions)
+        return out
+
+    def state(self, field: int) -> np.ndarray:
+        n = 3 * self.H if field == LINK_RES else self.H
+        a = np.zeros(n, np.int32)
+        _check(lib().dc_query_state(self.h, field, _p(a, _i32p), n), "dc_query_state")
+        return a
+
+    def rank_hosts(self, q: Dict[str, np.ndarray], pod: int, host_of: np.ndarray):
+        r = _Req(q)
+        ho = np.ascontiguousarray(host_of, np.int32)
+        feas = np.zeros(self.H, np.int32)
+        s32 = np.zeros(self.H, np.float32)
+        s64 = np.zeros(self.H, np.float64)
+        crit = np.zeros(self.H * self.n_criteria, np.int32)
+        nv = _check(lib().dc_rank_hosts(self.h, C.byref(r.s), pod, _p(ho, _i32p), _p(feas, _i32p),
+                                        _p(s32, _f32p), _p(s64, _f64p), _p(crit, _i32p)),
+                    "dc_rank_hosts")
+        return feas.astype(bool), s32, s64, crit.reshape(self.H, self.n_criteria), nv
+
+    def reset(self) -> None:
+        _check(lib().dc_reset(self.h), "dc_reset")
+        self._reqs = []
+
+
+def _handles(dcs: Sequence[DataCenter]):
+    arr = (C.c_void_p * len(dcs))(*[d.h.value for d in dcs])
+    return arr
+
+
+def schedule(dcs: Sequence[DataCenter], flags: int = SCHED_SYNC) -> None:
+    _check(lib().dc_schedule(_handles(dcs), len(dcs), flags), "dc_schedule")
+
+
+class Plan:
+    """A prepared batched launch (dc_plan)."""
+
+    def __init__(self, dcs: Sequence[DataCenter], flags: int = 0):
+        self.dcs = list(dcs)
+        h = C.c_void_p()
+        _check(lib().dc_plan_create(_handles(self.dcs), len(self.dcs), flags, C.byref(h)),
+               "dc_plan_create")
+        self.h = h
+
+    def launch(self, stream=None) -> None:
+        _check(lib().dc_plan_launch(self.h, _stream_handle(stream)), "dc_plan_launch")
+
+    def collect(self) -> None:
+        _check(lib().dc_plan_collect(self.h), "dc_plan_collect")
+
+    def stats(self):
+        d, hr, kc = C.c_int64(), C.c_int64(), C.c_int32()
+        _check(lib().dc_plan_stats(self.h, C.byref(d), C.byref(hr), C.byref(kc)), "dc_plan_stats")
+        return d.value, hr.value, kc.value
+
+    def close(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.dc_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+
+def load_instance(inst, stream=None, max_requests: Optional[int] = None) -> DataCenter:
+    """Creates a DataCenter for a workloads.Instance and submits its FCFS
+    stream of operations (schedules and releases)."""
+    dc = DataCenter.from_instance(inst, stream=stream)
+    R = inst.reqs.n if max_requests is None else min(max_requests, inst.reqs.n)
+    ops = inst.ops if inst.ops is not None else [(0, r) for r in range(inst.reqs.n)]
+    for kind, r in ops:
+        if r >= R:
+            if kind == 0:
+                break
+            continue
+        if kind == 0:
+            dc.submit(inst.reqs.request(r))
+        else:
+            dc.release(r)
+    return dc
