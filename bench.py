@@ -1,0 +1,389 @@
+#!/usr/bin/env python3
+"""Benchmark of the GPU network-aware multi-criteria container scheduler.
+
+Workload (default): 256 fat-tree data centers resident on the device, k
+cycling over {8, 16, 24, 32} (819,200 hosts in total), each receiving 100
+FCFS requests of 4-256 containers (singleton pods, Erdos-Renyi p=0.1 links,
+log-uniform 1-1000 Mbps), 0-70 % random pre-load, TOPSIS over 6 criteria.
+One step schedules every request of every instance from the pre-loaded
+state, in one batched launch (one kernel per fat-tree size, one thread block
+per data center) replayed from a CUDA graph.
+
+Printed (rank 0, one JSON line): host-rankings/s of the whole job (pod
+decisions x hosts ranked per decision), requests/s, p50/p99 request
+completion latency inside the batched launch, the same work scheduled one
+request per launch, the end-to-end rate through the C-ABI with host buffers,
+the roofline of the scheduling kernel and the FP64 oracle timed on the
+host's cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import glob
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = ("host-rankings/sec and requests/sec (p50/p99 latency) at oracle-exact placements "
+          "vs plain launch")
+UNIT = "host-rankings/s"
+BYTES_PER_HOST_RANKING = 16  # 4 int32 words of host state per host per decision
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--requests", type=int, default=100, help="requests per data center")
+    ap.add_argument("--instances", type=int, default=256)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def workload(args, rank):
+    from paper_1909_07673_gb300 import workloads as W
+    return W.batched(seed=4 + 1000 * rank, n_instances=args.instances, n_requests=args.requests)
+
+
+def config_dict(args, wl, world):
+    hosts = sum(i.hosts for i in wl.instances)
+    return {
+        "workload": "batched fat-tree DCs: %d instances (k 8/16/24/32), %d requests of 4-256 "
+                    "containers each, TOPSIS, 6 criteria" % (args.instances, args.requests),
+        "instances_per_gpu": args.instances,
+        "requests_per_gpu": args.instances * args.requests,
+        "hosts_per_gpu": hosts,
+        "method": "TOPSIS",
+        "l2": "flushed before every step (256 MiB device write); request inputs exceed L2",
+        "parallelism": "data centers sharded over %d rank(s), no collective" % world,
+    }
+
+
+# ----------------------------------------------------------------- oracle (CPU)
+
+def oracle_sample(wl, seconds):
+    """Runs the FP64 oracle (single thread) over leading requests of a
+    rotating set of instances until `seconds` pass; returns
+    (host_rankings, wall_s, description)."""
+    import oracle as O
+
+    t0 = time.perf_counter()
+    hr = 0
+    reqs = 0
+    used = []
+    i = 0
+    # one instance of each size first, then more, 2 requests at a time
+    while time.perf_counter() - t0 < seconds and i < len(wl.instances):
+        inst = wl.instances[i]
+        dc = O.OracleDC.from_instance(inst)
+        r = 0
+        while r < inst.reqs.n and time.perf_counter() - t0 < seconds and r < 2:
+            out = dc.schedule(inst.reqs.request(r))
+            hr += out["n_decisions"] * inst.hosts
+            reqs += 1
+            r += 1
+        used.append((inst.k, r))
+        i += 1
+    wall = time.perf_counter() - t0
+    desc = "oracle.c single thread, first %s requests of %d instances (k=%s), %.1f s" % (
+        "1-2", len(used), sorted(set(k for k, _ in used)), wall)
+    return hr, wall, desc, reqs
+
+
+def run_reference(args):
+    """The reference arm: the FP64 oracle timed on the host's cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle as O
+
+    O.build_oracle()
+    wl = workload(args, 0)
+    per = max(1.0, args.cpu_seconds / max(1, args.steps))
+    times, hrs = [], []
+    for s in range(args.warmup + args.steps):
+        hr, wall, desc, reqs = oracle_sample(wl, per)
+        if s >= args.warmup:
+            times.append(wall)
+            hrs.append(hr)
+    value = sum(hrs) / sum(times)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(args, wl, 1),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ----------------------------------------------------------------- clocks
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for n, v in zip(names, r[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                pass
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- helpers
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1909_07673_gb300", "csrc", "*"))):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(host_rankings_per_launch):
+    """DRAM bytes per launch of the scheduling kernel from the committed ncu
+    summary, scaled to this launch's host rankings; None when the summary is
+    missing or was taken on different kernel sources."""
+    p = os.path.join(ROOT, "profiles", "k_schedule_traffic.json")
+    try:
+        with open(p) as f:
+            t = json.load(f)
+    except Exception:
+        return None
+    if t.get("source_hash") != kernel_source_hash():
+        return None
+    return t["dram_bytes"] / t["host_rankings"] * host_rankings_per_launch
+
+
+# ----------------------------------------------------------------- ours
+
+def run_ours(args):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1909_07673_gb300 import dcsched as ds
+
+    wl = workload(args, rank)
+    stream = torch.cuda.Stream()
+    dcs = [ds.load_instance(inst, stream=stream) for inst in wl.instances]
+    plan = ds.Plan(dcs, ds.PLAN_GRAPH | ds.PLAN_RESET)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def step():
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        plan.launch(stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        for i in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            ev[i][0].record(stream)
+            plan.launch(stream)
+            ev[i][1].record(stream)
+        t1.record(stream)
+        torch.cuda.synchronize()
+    ms_step = t0.elapsed_time(t1) / args.steps
+    ms_kernel = statistics.mean(a.elapsed_time(b) for a, b in ev)
+    plan.collect()
+    dec, hr, nkern, start_ns = plan.stats()
+    n_req = sum(inst.reqs.n for inst in wl.instances)
+    lat = []
+    accepted = 0
+    for dc, inst in zip(dcs, wl.instances):
+        for r in range(inst.reqs.n):
+            st, nd, done = dc.status(r)
+            lat.append((done - start_ns) * 1e-6)
+            accepted += st == ds.ACCEPTED
+    t_max = torch.tensor([ms_step, ms_kernel], dtype=torch.float64, device="cuda")
+    if dist:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    ms_step, ms_kernel = float(t_max[0]), float(t_max[1])
+
+    # one request per launch on a sample (one instance per size, 8 requests)
+    plain_hr, plain_req, plain_s = 0, 0, 0.0
+    for inst in wl.instances[:4]:
+        dc = ds.DataCenter.from_instance(inst, stream=stream)
+        t = time.perf_counter()
+        for r in range(min(8, inst.reqs.n)):
+            dc.submit(inst.reqs.request(r))
+            ds.schedule([dc])
+            st, nd, _ = dc.status(r)
+            plain_hr += nd * inst.hosts
+            plain_req += 1
+        plain_s += time.perf_counter() - t
+        dc.close()
+
+    # end to end through the C-ABI with host buffers: submit every request
+    # (host copies), schedule (inputs host->device, kernels, results
+    # device->host), read a result
+    from paper_1909_07673_gb300.dcsched import _Req, _Request, lib as _lib
+    import ctypes as C
+    batches = []
+    for inst in wl.instances:
+        reqs = [_Req(inst.reqs.request(r)) for r in range(inst.reqs.n)]
+        batches.append((reqs, (_Request * len(reqs))(*[q.s for q in reqs])))
+    io0 = [dc.io_stats() for dc in dcs]
+    e2e_times = []
+    for s in range(1 + args.e2e_steps):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for dc, (reqs, arr) in zip(dcs, batches):
+            ds._check(_lib().dc_reset(dc.h), "dc_reset")
+            ds._check(_lib().dc_submit_batch(dc.h, len(reqs), arr, None), "dc_submit_batch")
+        ds.schedule(dcs)
+        dcs[0].status(0)
+        if s > 0:
+            e2e_times.append(time.perf_counter() - t)
+        else:
+            io0 = [dc.io_stats() for dc in dcs]
+    io1 = [dc.io_stats() for dc in dcs]
+    h2d = sum(b[0] - a[0] for a, b in zip(io0, io1)) / args.e2e_steps
+    d2h = sum(b[1] - a[1] for a, b in zip(io0, io1)) / args.e2e_steps
+    e2e_value = world * hr / statistics.mean(e2e_times)
+
+    peak, peak_kind = measured_peak()
+    achieved = hr * BYTES_PER_HOST_RANKING / (ms_kernel * 1e-3) / 1e9
+    traffic = ncu_traffic(hr)
+    if rank != 0:
+        if dist:
+            dist.barrier()
+        return 0
+    cpu_hr, cpu_s, cpu_desc, _ = oracle_sample(wl, args.cpu_seconds)
+    lat.sort()
+    line = {
+        "metric": METRIC, "value": world * hr / (ms_step * 1e-3), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": config_dict(args, wl, world),
+        "host_rankings_per_step": world * hr, "decisions_per_step": world * dec,
+        "requests_per_s": world * n_req / (ms_step * 1e-3),
+        "decisions_per_s": world * dec / (ms_step * 1e-3),
+        "accepted_fraction": accepted / n_req,
+        "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[int(len(lat) * 0.99)],
+                       "note": "request completion time from the start of the batched launch"},
+        "plain_launch": {"host_rankings_per_s": plain_hr / plain_s,
+                         "requests_per_s": plain_req / plain_s,
+                         "sample": "one request per launch (submit, schedule, sync, read) on the "
+                                   "first 8 requests of one instance per fat-tree size"},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": args.steps * nkern,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_kind": peak_kind + " (STREAM-style copy)",
+                     "note": "16 B of host state per host ranking over the scheduling launch "
+                             "(graph: state reset + one kernel per fat-tree size)"},
+        "cpu_baseline": {"value": cpu_hr / cpu_s, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": cpu_desc},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

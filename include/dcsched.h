@@ -118,6 +118,7 @@ typedef struct {
                           to the host of dst, -1 padded */
   double* pod_score;   /* [n_pods] FP64 score of the chosen host (oracle
                           arithmetic), -1 for pods not placed */
+  int64_t done_ns;     /* device clock (ns) when the request finished */
 } dc_result;
 
 /* Creates a data center on the current CUDA device.  cuda_stream: the
@@ -133,6 +134,11 @@ void dc_destroy(dc_t* dc);
  * submission order).  Validates and copies the arrays; no device work.
  * *req_id receives 0, 1, 2, ... in submission order. */
 int dc_submit_request(dc_t* dc, const dc_request* req, int64_t* req_id);
+
+/* Submits n requests in order (as n calls of dc_submit_request); req_ids[n]
+ * may be NULL.  Stops at the first invalid request and returns its error;
+ * the requests before it stay submitted. */
+int dc_submit_batch(dc_t* dc, int32_t n, const dc_request* reqs, int64_t* req_ids);
 
 /* Queues the departure of request req_id after everything submitted so far:
  * when reached, an accepted request returns its CPU, memory and bandwidth
@@ -183,9 +189,14 @@ int dc_plan_create(dc_t* const* dcs, int32_t n, int32_t flags, dc_plan** out);
 int dc_plan_launch(dc_plan* plan, void* cuda_stream);
 int dc_plan_collect(dc_plan* plan);
 /* Totals of the last collected launch: pod decisions and host rankings
- * (decisions x hosts), and the number of kernels one launch runs. */
+ * (decisions x hosts), the number of kernels one launch runs, and the
+ * device clock (ns) at which its first block started. */
 int dc_plan_stats(dc_plan* plan, int64_t* decisions, int64_t* host_rankings,
-                  int32_t* kernels_per_launch);
+                  int32_t* kernels_per_launch, int64_t* start_ns);
+
+/* Bytes copied host -> device (request inputs) and device -> host (results)
+ * by this instance since dc_create. */
+int dc_io_stats(dc_t* dc, int64_t* h2d_bytes, int64_t* d2h_bytes);
 void dc_plan_destroy(dc_plan* plan);
 
 /* Human-readable text of an error code (static storage). */

@@ -9,22 +9,28 @@
 //
 //   setup    (warp 0)  pod demand (sums of c^min / c^max), the pod's links to
 //                      containers of earlier pods, per-edge-switch and
-//                      per-pod neighbour counts, a host -> link-count hash [a1]
+//                      per-pod neighbour counts, a host -> link-count hash;
+//                      runs at the end of the previous pod's commit, with the
+//                      records of the following pod prefetched into
+//                      registers                                          [a1]
 //   tables   (block)   for every edge switch e, the smallest bottleneck
 //                      min(uplink(v), best switch path e -> edge(v)) over the
 //                      placed neighbours v and the smallest slack against
 //                      their bw^min, each with its host and the runner-up
-//                      over other hosts (a neighbour host excludes itself) [a2, a3]
+//                      over other hosts (a neighbour host excludes itself);
+//                      the aggregation-core part is shared between the
+//                      lanes of one pod by warp shuffles                 [a2, a3]
 //   stats    (block)   viability and criteria of every host; exact integer
 //                      column statistics over the viable hosts (count, sum,
 //                      sum of squares, max, min) by warp redux + one
 //                      cross-warp pass; FP32 per-column constants         [a4]
 //   score    (block)   FP32 score of every viable host (TOPSIS closeness or
 //                      AHP global priority), kept in registers            [a5]
-//   pick     (block)   top-2 argmax (lowest index on ties); certification:
-//                      hosts within a relative guard band of the maximum
-//                      are re-scored with the FP64 expression of the
-//                      oracle unless they carry the leader's criteria     [a6]
+//   pick     (block)   top-2 argmax (lowest index on ties), finished by the
+//                      last warp to arrive; certification: hosts within a
+//                      relative guard band of the maximum are re-scored
+//                      with the FP64 expression of the oracle unless they
+//                      carry the leader's criteria                        [a6]
 //   commit   (warp 0)  widest shortest path per link to a placed neighbour
 //                      (warp-parallel over the (a, c) candidates), bandwidth
 //                      and capacity reservation; on failure undo, mask the
@@ -55,21 +61,27 @@ namespace dcs {
 struct Ctx {
   // instance
   int32_t k, half, H, E, C, method, link_mbps;
+  int32_t gs;             // lanes per pod group in the table pass (pow2 >= half)
+  int32_t ea0, ac0, ld;   // link slots: edge-agg base, agg-core base, row stride
   unsigned long long mh;  // ceil(2^32 / half): x / half == (x * mh) >> 32
   double W[kMaxC], L1[kMaxC];
   float Wf[kMaxC], L1f[kMaxC];
-  int4* scr_pe;
   // request
   int64_t c_off, e_off, p_off, l_off;
   int32_t n_c, n_e, n_p;
   const int32_t* pc;  // pod -> container range (shared or global)
   const int32_t* pe;  // pod -> link range
   int32_t* hof;       // container -> host (shared copy, or the global output)
+  int4* pel;          // peer links of the current pod (shared, or global scratch)
   // pod
   long long dmin_cpu, dmax_cpu, dmin_mem, dmax_mem;
   int32_t size, npe;
   int32_t need1, need1h, need2;
   int32_t hash_ok;
+  int32_t nfail;
+  // commit prefilter (exact necessary condition, see commit_possible)
+  long long bw_total;  // sum of bw_min over the pod's links to placed containers
+  int32_t n_over, h_over;  // neighbour hosts whose uplink cannot carry their links
   // column statistics over the viable hosts
   int32_t n;
   long long S1[kMaxC], S2[kMaxC];
@@ -83,25 +95,27 @@ struct Ctx {
   int32_t idx1;
   int32_t winner;
   int32_t commit_ok;
+  int32_t arrive;
   int32_t ndec;
-  int32_t placed;
 };
 
 struct Sm {
   Ctx* c;
   uint32_t* cm;   // [H] free cpu | free mem << 16
   int32_t* ctr;   // [H] container count | kPreBit
-  int32_t* res;   // [3H] link residuals (numbering of dcsched.h)
+  int32_t* lk;    // link residuals, layout of link_slots()
   int32_t *T1, *T1h, *T2, *S1, *S1h, *S2, *Be;  // [E] per edge switch
   int32_t* Cp;    // [k] per pod
-  int32_t* G;     // [kChunk * k * half]
   uint32_t* tmark;    // [B] bit j of word t: host t + j*B hosts a neighbour
   uint32_t* trymask;  // [B] bit j of word t: host t + j*B failed a commit
   int32_t *hkey, *hcnt;  // [kHash]
+  long long* hsum;       // [kHash] sum of bw_min of the links to that host
   long long* red64;
   int32_t* red32;
   unsigned char* sel;
   int32_t *st_pc, *st_pe, *st_hof;
+  int4* pel;
+  int4* curc;  // [32] container records of the pod being placed
 };
 
 static __device__ __forceinline__ Sm carve(unsigned char* base, int k, int B) {
@@ -110,36 +124,56 @@ static __device__ __forceinline__ Sm carve(unsigned char* base, int k, int B) {
   s.c = reinterpret_cast<Ctx*>(base + L.ctx);
   s.cm = reinterpret_cast<uint32_t*>(base + L.cm);
   s.ctr = reinterpret_cast<int32_t*>(base + L.ctr);
-  s.res = reinterpret_cast<int32_t*>(base + L.res);
+  s.lk = reinterpret_cast<int32_t*>(base + L.lk);
   const int E = k * k / 2;
   int32_t* t = reinterpret_cast<int32_t*>(base + L.tab);
   s.T1 = t; s.T1h = t + E; s.T2 = t + 2 * E; s.S1 = t + 3 * E; s.S1h = t + 4 * E;
   s.S2 = t + 5 * E; s.Be = t + 6 * E;
   s.Cp = reinterpret_cast<int32_t*>(base + L.cp);
-  s.G = reinterpret_cast<int32_t*>(base + L.g);
   s.tmark = reinterpret_cast<uint32_t*>(base + L.tmark);
   s.trymask = reinterpret_cast<uint32_t*>(base + L.trymask);
   s.hkey = reinterpret_cast<int32_t*>(base + L.hkey);
   s.hcnt = reinterpret_cast<int32_t*>(base + L.hcnt);
+  s.hsum = reinterpret_cast<long long*>(base + L.hsum);
   s.red64 = reinterpret_cast<long long*>(base + L.red64);
   s.red32 = reinterpret_cast<int32_t*>(base + L.red32);
   s.sel = base + L.sel;
   s.st_pc = reinterpret_cast<int32_t*>(base + L.st_pc);
   s.st_pe = reinterpret_cast<int32_t*>(base + L.st_pe);
   s.st_hof = reinterpret_cast<int32_t*>(base + L.st_hof);
+  s.pel = reinterpret_cast<int4*>(base + L.pel);
+  s.curc = reinterpret_cast<int4*>(base + L.curc);
   return s;
 }
 
 // ---------------------------------------------------------------- helpers
 
 static __device__ __forceinline__ int lane_id() { return threadIdx.x & 31; }
+static __device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
 static __device__ __forceinline__ int imin(int a, int b) { return a < b ? a : b; }
 static __device__ __forceinline__ int imax(int a, int b) { return a > b ? a : b; }
 static __device__ __forceinline__ int div_half(const Ctx& c, int x) {
   return (int)(((unsigned long long)(unsigned)x * c.mh) >> 32);
 }
 
-// link ids (numbering of dcsched.h)
+// shared-memory slots of links (see link_slots())
+static __device__ __forceinline__ int s_ea(const Ctx& c, int e, int a) { return c.ea0 + a * c.ld + e; }
+static __device__ __forceinline__ int s_ac(const Ctx& c, int ag, int cc) { return c.ac0 + cc * c.ld + ag; }
+// global link id -> shared slot
+static __device__ __forceinline__ int lslot(const Ctx& c, int l) {
+  if (l < c.H) return l;
+  if (l < 2 * c.H) {
+    const int t = l - c.H, e = div_half(c, t);
+    return s_ea(c, e, t - e * c.half);
+  }
+  const int t = l - 2 * c.H, ag = div_half(c, t);
+  return s_ac(c, ag, t - ag * c.half);
+}
+// global link ids (numbering of dcsched.h)
 static __device__ __forceinline__ int l_ea(const Ctx& c, int e, int a) { return c.H + e * c.half + a; }
 static __device__ __forceinline__ int l_ac(const Ctx& c, int p, int a, int cc) {
   return 2 * c.H + (p * c.half + a) * c.half + cc;
@@ -160,25 +194,50 @@ static __device__ __forceinline__ Top2 max2_combine(Top2 a, Top2 b) {
 }
 
 static __device__ __forceinline__ uint32_t hash_host(int h) {
-  return ((uint32_t)h * 2654435761u) >> 22;  // 10 bits = kHash slots
+  return ((uint32_t)h * 2654435761u) >> 24;  // 8 bits = kHash slots
+}
+
+// Hash slot of neighbour host u (-1 if u hosts none of the pod's placed
+// neighbours); only valid while c.hash_ok.
+static __device__ __forceinline__ int peer_slot(const Sm& s, int u) {
+  uint32_t slot = hash_host(u);
+  for (int p = 0; p < kHash; ++p) {
+    const int key = s.hkey[slot];
+    if (key == u) return (int)slot;
+    if (key == -1) return -1;
+    slot = (slot + 1) & (kHash - 1);
+  }
+  return -1;
 }
 
 // number of the pod's links whose placed end is on host u
 static __device__ int peer_links_on(const Sm& s, int u) {
   const Ctx& c = *s.c;
   if (c.hash_ok) {
-    uint32_t slot = hash_host(u);
-    for (int p = 0; p < kHash; ++p) {
-      const int key = s.hkey[slot];
-      if (key == u) return s.hcnt[slot];
-      if (key == -1) return 0;
-      slot = (slot + 1) & (kHash - 1);
-    }
-    return 0;
+    const int slot = peer_slot(s, u);
+    return slot < 0 ? 0 : s.hcnt[slot];
   }
   int n = 0;
-  for (int i = 0; i < c.npe; ++i) n += (c.scr_pe[i].y == u);
+  for (int i = 0; i < c.npe; ++i) n += (c.pel[i].y == u);
   return n;
+}
+
+// Exact necessary condition for the commit of the pod on u to succeed
+// (used only to skip candidates whose commit must fail, which leaves the
+// first successful candidate unchanged): every path from u to a neighbour
+// on another host starts with u's host link and every path to neighbour v
+// ends with v's host link, and each link reserves at least bw^min.
+template <int B>
+static __device__ __forceinline__ bool commit_possible(const Sm& s, int u) {
+  const Ctx& c = *s.c;
+  if (c.npe == 0 || !c.hash_ok) return true;
+  if (c.n_over > 1 || (c.n_over == 1 && u != c.h_over)) return false;
+  long long on_u = 0;
+  if ((s.tmark[u % B] >> (u / B)) & 1u) {
+    const int slot = peer_slot(s, u);
+    if (slot >= 0) on_u = s.hsum[slot];
+  }
+  return (long long)s.lk[u] >= c.bw_total - on_u;
 }
 
 // Criteria of host u (integers, all benefit criteria) and its viability.
@@ -192,7 +251,7 @@ static __device__ __forceinline__ bool host_crit(const Sm& s, int u, int32_t* x)
   const uint32_t cm = s.cm[u];
   const int cpu = (int)(cm & 0xffffu), mem = (int)(cm >> 16);
   const int ctr = s.ctr[u];
-  const int up = s.res[u];
+  const int up = s.lk[u];
   bool f = cpu >= c.dmin_cpu && mem >= c.dmin_mem;
   x[0] = cpu;
   x[1] = mem;
@@ -232,10 +291,13 @@ static __device__ __forceinline__ bool same_vec(const int32_t* a, const int32_t*
   return eq;
 }
 
-// FP32 fast-path score.  TOPSIS: differences to the ideal / anti-ideal are
-// formed exactly in integers, scaled by q_v = W_v / sqrt(sum x^2) and
-// accumulated with FMA; relative error <= 19 * 2^-24 against the exact
-// closeness.  AHP RATIO: sum_v L1_v (x_v + 1) / T_v, error <= 11 * 2^-24.
+// FP32 fast-path selection score.  TOPSIS: the squared distances to the
+// ideal and anti-ideal, dp and dn, are formed from exact integer differences
+// scaled by q_v = W_v / sqrt(sum x^2) and accumulated with FMA; the score is
+// dn / (dp + dn), which orders hosts exactly like the closeness
+// Dn / (Dp + Dn) (both decrease with dp / dn) and needs no square root.  Its
+// relative error is <= 33 * 2^-24.  AHP RATIO: sum_v L1_v (x_v + 1) / T_v,
+// relative error <= 11 * 2^-24.
 static __device__ __forceinline__ float score32(const Ctx& c, const int32_t* x) {
   if (c.method == DC_TOPSIS) {
     float dp = 0.f, dn = 0.f;
@@ -248,15 +310,29 @@ static __device__ __forceinline__ float score32(const Ctx& c, const int32_t* x) 
         dn = __fmaf_rn(b, b, dn);
       }
     }
-    const float Dp = __fsqrt_rn(dp), Dn = __fsqrt_rn(dn);
-    const float s = __fadd_rn(Dp, Dn);
-    return s == 0.f ? 1.f : __fdiv_rn(Dn, s);
+    const float s = __fadd_rn(dp, dn);
+    return s == 0.f ? 1.f : __fdividef(dn, s);
   }
   float acc = 0.f;
 #pragma unroll
   for (int v = 0; v < kMaxC; ++v)
     if (v < c.C) acc = __fmaf_rn(c.L1f[v], __fmul_rn((float)(x[v] + 1), c.invTf[v]), acc);
   return acc;
+}
+
+// FP32 TOPSIS closeness Dn / (Dp + Dn) itself (reported by the ranking API).
+static __device__ __forceinline__ float closeness32(const Ctx& c, const int32_t* x) {
+  if (c.method != DC_TOPSIS) return score32(c, x);
+  float dp = 0.f, dn = 0.f;
+  for (int v = 0; v < c.C; ++v) {
+    const float a = (float)(x[v] - c.mx[v]) * c.qf[v];
+    const float b = (float)(x[v] - c.mn[v]) * c.qf[v];
+    dp = __fmaf_rn(a, a, dp);
+    dn = __fmaf_rn(b, b, dn);
+  }
+  const float Dp = __fsqrt_rn(dp), Dn = __fsqrt_rn(dn);
+  const float s = __fadd_rn(Dp, Dn);
+  return s == 0.f ? 1.f : __fdiv_rn(Dn, s);
 }
 
 // FP64 per-column constants with the oracle's operations: TOPSIS norm
@@ -304,14 +380,33 @@ static __device__ __noinline__ double score64(int method, int C, const double* W
 
 // ---------------------------------------------------------------- phases
 
+// Records of one pod prefetched by warp 0 lane-wise (first 32 containers and
+// first 32 links of the pod's groups).
+struct Pre { int4 c, e; };
+
+static __device__ __forceinline__ Pre prefetch_pod(const Ctx& c, const InstDev& I, int g) {
+  const int lane = lane_id();
+  Pre p = {make_int4(0, 0, 0, 0), make_int4(0, 0, 0, 0)};
+  if (g < c.n_p) {
+    const int c0 = c.pc[g], c1 = c.pc[g + 1], e0 = c.pe[g], e1 = c.pe[g + 1];
+    if (c0 + lane < c1) p.c = I.c_lay[c.c_off + c0 + lane];
+    if (e0 + lane < e1) p.e = I.e_lay[c.e_off + e0 + lane];
+  }
+  return p;
+}
+
 // a1: pod demand and the pod's links to containers of earlier pods (warp 0).
-static __device__ void pod_setup_warp(const Sm& s, const InstDev& I, int g) {
+// `cur` holds the pod's prefetched records; on return `cur` holds those of
+// pod g + 1.
+template <int B>
+static __device__ void pod_setup_warp(const Sm& s, const InstDev& I, int g, Pre& cur) {
   Ctx& c = *s.c;
   const int lane = lane_id();
   const int32_t c0 = c.pc[g], c1 = c.pc[g + 1];
   long long dmin_c = 0, dmax_c = 0, dmin_m = 0, dmax_m = 0;
   for (int pos = c0 + lane; pos < c1; pos += 32) {
-    const int4 q = I.c_lay[c.c_off + pos];
+    const int4 q = pos - c0 < 32 ? cur.c : I.c_lay[c.c_off + pos];
+    if (pos - c0 < 32) s.curc[lane] = q;
     dmin_c += q.y & 0xffff;
     dmax_c += (unsigned)q.y >> 16;
     dmin_m += q.z & 0xffff;
@@ -333,23 +428,25 @@ static __device__ void pod_setup_warp(const Sm& s, const InstDev& I, int g) {
     int4 q = make_int4(0, 0, 0, 0);
     int hv = 0;
     if (pos < e1) {
-      q = I.e_lay[c.e_off + pos];
+      q = base == e0 ? cur.e : I.e_lay[c.e_off + pos];
       peer = !(q.x & kLinkIntra);
       if (peer) hv = c.hof[q.y];
     }
     const unsigned m = __ballot_sync(0xffffffffu, peer);
     if (peer) {
       const int slot = npe + __popc(m & ((1u << lane) - 1u));
-      c.scr_pe[slot] = make_int4(q.x, hv, q.z, q.w);
+      c.pel[slot] = make_int4(q.x, hv, q.z, q.w);
       const int ev = div_half(c, hv);
       atomicAdd(&s.Be[ev], 1);
       atomicAdd(&s.Cp[div_half(c, ev)], 1);
+      atomicOr(&s.tmark[hv % B], 1u << (hv / B));
       uint32_t h = hash_host(hv);
       bool ins = false;
       for (int p = 0; p < kHash / 2; ++p) {  // bounded probing
         const int old = atomicCAS(&s.hkey[h], -1, hv);
         if (old == -1 || old == hv) {
           atomicAdd(&s.hcnt[h], 1);
+          atomicAdd((unsigned long long*)&s.hsum[h], (unsigned long long)q.z);
           ins = true;
           break;
         }
@@ -366,6 +463,26 @@ static __device__ void pod_setup_warp(const Sm& s, const InstDev& I, int g) {
     nd = max2_combine(nd, other);
   }
   hash_ok = __all_sync(0xffffffffu, hash_ok);
+  __syncwarp();
+  // neighbour hosts whose own uplink cannot carry the pod's links to them
+  long long tot = 0;
+  int n_over = 0, h_over = -1;
+  if (npe > 0)
+    for (int h = lane; h < kHash; h += 32) {
+      const int key = s.hkey[h];
+      if (key >= 0) {
+        tot += s.hsum[h];
+        if (s.hsum[h] > (long long)s.lk[key]) {
+          ++n_over;
+          h_over = key;
+        }
+      }
+    }
+  for (int o = 16; o > 0; o >>= 1) {
+    tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    n_over += __shfl_xor_sync(0xffffffffu, n_over, o);
+    h_over = imax(h_over, __shfl_xor_sync(0xffffffffu, h_over, o));
+  }
   if (lane == 0) {
     c.dmin_cpu = dmin_c;
     c.dmax_cpu = dmax_c;
@@ -377,70 +494,84 @@ static __device__ void pod_setup_warp(const Sm& s, const InstDev& I, int g) {
     c.need1h = nd.h1;
     c.need2 = nd.v2;
     c.hash_ok = hash_ok ? 1 : 0;
+    c.nfail = 0;
+    c.bw_total = tot;
+    c.n_over = n_over;
+    c.h_over = h_over;
   }
+  cur = prefetch_pod(c, I, g + 1);
+  __syncwarp();
 }
 
-// marks the hosts of placed neighbours (block-wide, after setup)
+// Undoes the pod's neighbour bookkeeping (warp 0, end of a pod).
 template <int B>
-static __device__ void mark_peers(const Sm& s) {
+static __device__ void pod_clear_warp(const Sm& s) {
   const Ctx& c = *s.c;
-  for (int i = threadIdx.x; i < c.npe; i += B) {
-    const int hv = c.scr_pe[i].y;
-    atomicOr(&s.tmark[hv % B], 1u << (hv / B));
+  const int lane = lane_id();
+  for (int i = lane; i < c.npe; i += 32) {
+    const int hv = c.pel[i].y;
+    const int ev = div_half(c, hv);
+    s.Be[ev] = 0;
+    s.Cp[div_half(c, ev)] = 0;
+    s.tmark[hv % B] = 0u;
   }
+  if (c.npe > 0)
+    for (int h = lane; h < kHash; h += 32) {
+      s.hkey[h] = -1;
+      s.hcnt[h] = 0;
+      s.hsum[h] = 0;
+    }
+  if (c.nfail > 0)
+    for (int t = lane; t < B; t += 32) s.trymask[t] = 0u;
 }
 
 // a2/a3 tables: T'_v[e] = min(uplink(v), best switch-path bottleneck from
 // edge switch e to edge(v)) folded over the pod's placed neighbours v.
+// Lanes are grouped per pod (gs lanes, lane a of a group = aggregation a);
+// each lane computes max_c min(ac(p, a, c), ac(pod(v), a, c)) for its a and
+// the group shares the values by shuffles.  Ends with a barrier.
 template <int B>
 static __device__ void build_tables(const Sm& s) {
   const Ctx& c = *s.c;
-  const int tid = threadIdx.x;
-  const int half = c.half, k = c.k, E = c.E;
-  for (int base = 0; base < c.npe; base += kChunk) {
-    const int nch = imin(kChunk, c.npe - base);
-    // G[i][p][a] = max_c min(ac(p, a, c), ac(pod(v_i), a, c))
-    const int per = k * half;
-    for (int idx = tid; idx < nch * per; idx += B) {
-      const int i = idx / per, rem = idx - i * per;
-      const int p = div_half(c, rem), a = rem - p * half;
-      const int pv = div_half(c, div_half(c, c.scr_pe[base + i].y));
-      int m = -1;
-      for (int cc = 0; cc < half; ++cc)
-        m = imax(m, imin(s.res[l_ac(c, p, a, cc)], s.res[l_ac(c, pv, a, cc)]));
-      s.G[idx] = m;
-    }
-    __syncthreads();
-    for (int e = tid; e < E; e += B) {
-      Top2 t = {s.T1[e], s.T1h[e], s.T2[e]};
-      Top2 sl = {s.S1[e], s.S1h[e], s.S2[e]};
-      const int pe_ = div_half(c, e);
-      for (int i = 0; i < nch; ++i) {
-        const int4 q = c.scr_pe[base + i];
-        const int v = q.y, need = q.z;
-        const int ev = div_half(c, v), pv = div_half(c, ev);
-        int mid;
-        if (e == ev) {
-          mid = kInf;
-        } else if (pe_ == pv) {
-          mid = -1;
-          for (int a = 0; a < half; ++a)
-            mid = imax(mid, imin(s.res[l_ea(c, e, a)], s.res[l_ea(c, ev, a)]));
-        } else {
-          mid = -1;
-          const int32_t* Gi = s.G + i * per + pe_ * half;
-          for (int a = 0; a < half; ++a)
-            mid = imax(mid, imin(imin(s.res[l_ea(c, e, a)], s.res[l_ea(c, ev, a)]), Gi[a]));
+  const int half = c.half, gs = c.gs, k = c.k;
+  const int lane = lane_id();
+  const int gbase = lane & ~(gs - 1);
+  for (int t0 = threadIdx.x - lane; t0 < k * gs; t0 += B) {
+    const int t = t0 + lane;
+    const int p = t / gs, a = t - p * gs;  // gs is a power of two
+    const bool active = t < k * gs && a < half;
+    const int e = p * half + a;
+    Top2 tt = {kInf, -1, kInf}, sl = {kInf, -1, kInf};
+    for (int i = 0; i < c.npe; ++i) {
+      const int4 q = c.pel[i];
+      const int v = q.y, need = q.z;
+      const int ev = div_half(c, v), pv = div_half(c, ev);
+      int gm = -1;
+      if (active && p != pv)
+        for (int cc = 0; cc < half; ++cc)
+          gm = imax(gm, imin(s.lk[s_ac(c, p * half + a, cc)], s.lk[s_ac(c, pv * half + a, cc)]));
+      int mid = -1;
+      for (int a2 = 0; a2 < half; ++a2) {
+        const int g2 = __shfl_sync(0xffffffffu, gm, gbase + a2);
+        if (active) {
+          int m = imin(s.lk[s_ea(c, e, a2)], s.lk[s_ea(c, ev, a2)]);
+          if (p != pv) m = imin(m, g2);
+          mid = imax(mid, m);
         }
-        const int T = imin(s.res[v], mid);
-        t = min2_combine(t, Top2{T, v, kInf});
+      }
+      if (active) {
+        if (e == ev) mid = kInf;
+        const int T = imin(s.lk[v], mid);
+        tt = min2_combine(tt, Top2{T, v, kInf});
         sl = min2_combine(sl, Top2{T - need, v, kInf});
       }
-      s.T1[e] = t.v1; s.T1h[e] = t.h1; s.T2[e] = t.v2;
+    }
+    if (active) {
+      s.T1[e] = tt.v1; s.T1h[e] = tt.h1; s.T2[e] = tt.v2;
       s.S1[e] = sl.v1; s.S1h[e] = sl.h1; s.S2[e] = sl.v2;
     }
-    __syncthreads();
   }
+  __syncthreads();
 }
 
 // a4: exact column statistics over the viable hosts and FP32 constants.
@@ -536,28 +667,21 @@ static __device__ void column_fp64(const Sm& s) {
   __syncthreads();
 }
 
-// a5: FP32 scores of the viable hosts owned by this thread (-1 otherwise).
-template <int B, int HPT>
-static __device__ __forceinline__ void score_pass(const Sm& s, float* sc) {
-  const Ctx& c = *s.c;
-  const int tid = threadIdx.x;
-#pragma unroll
-  for (int j = 0; j < HPT; ++j) {
-    sc[j] = -1.f;
-    const int u = tid + j * B;
-    if (u < c.H) {
-      int32_t x[kMaxC];
-      if (host_crit<B>(s, u, x)) sc[j] = score32(c, x);
-    }
-  }
-}
-
-// block-wide (max, lowest index, second distinct max) over FP32 scores
-struct Sel { float m1; int idx; float m2; };
+// block-wide (max, lowest index, number of hosts at the max, second
+// distinct max) over FP32 selection scores
+struct Sel { float m1; int idx; int cnt; float m2; };
 static __device__ __forceinline__ Sel sel_combine(Sel a, Sel b) {
-  if (a.m1 > b.m1) return {a.m1, a.idx, fmaxf(a.m2, b.m1)};
-  if (a.m1 < b.m1) return {b.m1, b.idx, fmaxf(b.m2, a.m1)};
-  return {a.m1, imin(a.idx, b.idx), fmaxf(a.m2, b.m2)};
+  if (a.m1 > b.m1) return {a.m1, a.idx, a.cnt, fmaxf(a.m2, b.m1)};
+  if (a.m1 < b.m1) return {b.m1, b.idx, b.cnt, fmaxf(b.m2, a.m1)};
+  return {a.m1, imin(a.idx, b.idx), a.cnt + b.cnt, fmaxf(a.m2, b.m2)};
+}
+static __device__ __forceinline__ Sel sel_warp(Sel me) {
+  for (int o = 16; o > 0; o >>= 1) {
+    Sel t = {__shfl_xor_sync(0xffffffffu, me.m1, o), __shfl_xor_sync(0xffffffffu, me.idx, o),
+             __shfl_xor_sync(0xffffffffu, me.cnt, o), __shfl_xor_sync(0xffffffffu, me.m2, o)};
+    me = sel_combine(me, t);
+  }
+  return me;
 }
 struct Sel64 { double s; int idx; };
 static __device__ __forceinline__ Sel64 sel64_combine(Sel64 a, Sel64 b) {
@@ -566,66 +690,73 @@ static __device__ __forceinline__ Sel64 sel64_combine(Sel64 a, Sel64 b) {
   return {a.s, imin(a.idx, b.idx)};
 }
 
-// a6: argmax over sc[] (hosts that failed a commit excluded) and
+// FP32 selection score of host u, or -1 when u is not viable, its commit
+// must fail, or it failed a commit already.
+template <int B>
+static __device__ __forceinline__ float cand_score(const Sm& s, int u, int32_t* x) {
+  if ((s.trymask[u % B] >> (u / B)) & 1u) return -1.f;
+  if (!host_crit<B>(s, u, x) || !commit_possible<B>(s, u)) return -1.f;
+  return score32(*s.c, x);
+}
+
+// a5/a6: FP32 scores of every candidate fused with the block argmax, then
 // certification.  Sets c.winner (-1 when no candidate remains).
-template <int B, int HPT>
-static __device__ void pick_host(const Sm& s, const float* sc) {
+template <int B>
+static __device__ void pick_host(const Sm& s) {
   Ctx& c = *s.c;
   const int tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
   constexpr int NW = B / 32;
-  const uint32_t tried = s.trymask[tid];
-  Sel me = {-1.f, INT_MAX, -1.f};
-#pragma unroll
-  for (int j = 0; j < HPT; ++j)
-    if (sc[j] >= 0.f && !((tried >> j) & 1u)) me = sel_combine(me, Sel{sc[j], tid + j * B, -1.f});
-  for (int o = 16; o > 0; o >>= 1) {
-    Sel t = {__shfl_xor_sync(0xffffffffu, me.m1, o), __shfl_xor_sync(0xffffffffu, me.idx, o),
-             __shfl_xor_sync(0xffffffffu, me.m2, o)};
-    me = sel_combine(me, t);
+  Sel me = {-1.f, INT_MAX, 0, -1.f};
+#pragma unroll 1
+  for (int u = tid; u < c.H; u += B) {
+    int32_t x[kMaxC];
+    const float sc = cand_score<B>(s, u, x);
+    if (sc >= 0.f) me = sel_combine(me, Sel{sc, u, 1, -1.f});
   }
+  me = sel_warp(me);
+  // the last warp to arrive finishes the block reduction
   Sel* ws = reinterpret_cast<Sel*>(s.sel);
-  if (lane == 0) ws[w] = me;
-  __syncthreads();
-  if (w == 0) {
-    Sel t = lane < NW ? ws[lane] : Sel{-1.f, INT_MAX, -1.f};
-    for (int o = 16; o > 0; o >>= 1) {
-      Sel q = {__shfl_xor_sync(0xffffffffu, t.m1, o), __shfl_xor_sync(0xffffffffu, t.idx, o),
-               __shfl_xor_sync(0xffffffffu, t.m2, o)};
-      t = sel_combine(t, q);
-    }
+  int last = 0;
+  if (lane == 0) {
+    ws[w] = me;
+    __threadfence_block();
+    last = atomicAdd(&c.arrive, 1) == NW - 1;
+  }
+  last = __shfl_sync(0xffffffffu, last, 0);
+  if (last) {
+    __threadfence_block();
+    Sel t = lane < NW ? ws[lane] : Sel{-1.f, INT_MAX, 0, -1.f};
+    t = sel_warp(t);
     if (lane == 0) {
       c.m1 = t.m1;
       c.idx1 = t.idx;
       c.m2 = t.m2;
       c.winner = t.m1 < 0.f ? -1 : t.idx;
+      c.arrive = t.cnt;  // hosts at the maximum (reset below)
     }
   }
   __syncthreads();
   const float m1 = c.m1;
-  if (m1 < 0.f) return;  // nothing viable left (c.winner == -1)
-  const int idx1 = c.idx1;
+  const int cnt1 = c.arrive;
   // guard band: every host whose FP64 score can reach the maximum has an
-  // FP32 score >= m1 * (1 - 2^-16) (the FP32 error is below 2e-6 relative)
+  // FP32 selection score >= m1 * (1 - 2^-16) (its error is below 2e-6
+  // relative)
   const float thr = __fsub_rn(m1, m1 * 0x1p-16f);
-  bool need_x1 = false;
-#pragma unroll
-  for (int j = 0; j < HPT; ++j)
-    need_x1 = need_x1 || (sc[j] >= thr && !((tried >> j) & 1u) && tid + j * B != idx1);
+  const bool band_clear = c.m2 < thr;
+  __syncthreads();
+  if (tid == 0) c.arrive = 0;
+  if (m1 < 0.f || (band_clear && cnt1 == 1)) return;  // none, or a unique leader
+  const int idx1 = c.idx1;
   int32_t x1[kMaxC];
-  if (need_x1) host_crit_slow<B>(s, idx1, x1);
-  bool full = !(c.m2 < thr);
+  host_crit_slow<B>(s, idx1, x1);
+  bool full = !band_clear;
   if (!full) {
-    // only hosts with exactly the leader's score are in the band: they are
-    // certified if they all carry the leader's criteria vector
+    // ties at the leader's score: certified if they all carry its criteria
     bool mism = false;
-#pragma unroll
-    for (int j = 0; j < HPT; ++j) {
-      const int u = tid + j * B;
-      if (sc[j] == m1 && !((tried >> j) & 1u) && u != idx1) {
-        int32_t x[kMaxC];
-        host_crit_slow<B>(s, u, x);
-        mism = mism || !same_vec(x, x1, c.C);
-      }
+#pragma unroll 1
+    for (int u = tid; u < c.H; u += B) {
+      int32_t x[kMaxC];
+      if (u != idx1 && cand_score<B>(s, u, x) == m1) mism = mism || !same_vec(x, x1, c.C);
     }
     full = __syncthreads_or(mism);
   }
@@ -635,15 +766,11 @@ static __device__ void pick_host(const Sm& s, const float* sc) {
   // index)
   column_fp64<B>(s);
   Sel64 b = {-1.0, INT_MAX};
-#pragma unroll
-  for (int j = 0; j < HPT; ++j) {
-    const int u = tid + j * B;
-    if (sc[j] >= thr && !((tried >> j) & 1u)) {
-      int32_t x[kMaxC];
-      host_crit_slow<B>(s, u, x);
-      if (u == idx1 || !same_vec(x, x1, c.C))
-        b = sel64_combine(b, Sel64{score64(c.method, c.C, c.W, c.L1, c.norm, c.Ap, c.An, c.Td, x), u});
-    }
+#pragma unroll 1
+  for (int u = tid; u < c.H; u += B) {
+    int32_t x[kMaxC];
+    if (cand_score<B>(s, u, x) >= thr && (u == idx1 || !same_vec(x, x1, c.C)))
+      b = sel64_combine(b, Sel64{score64(c.method, c.C, c.W, c.L1, c.norm, c.Ap, c.An, c.Td, x), u});
   }
   for (int o = 16; o > 0; o >>= 1) {
     Sel64 q = {__shfl_xor_sync(0xffffffffu, b.s, o), __shfl_xor_sync(0xffffffffu, b.idx, o)};
@@ -665,6 +792,7 @@ static __device__ void pick_host(const Sm& s, const float* sc) {
 
 // Widest shortest path between hosts hs != ht (warp-wide; every lane gets
 // the result).  Ties: lowest aggregation index a, then lowest core index c.
+// links[] receive global link ids.
 struct PathSel { int b, idx; };
 static __device__ __forceinline__ PathSel path_combine(PathSel a, PathSel b) {
   if (a.b > b.b) return a;
@@ -677,7 +805,7 @@ static __device__ int widest_path_warp(const Sm& s, int hs, int ht, int* links, 
   const int lane = lane_id();
   const int half = c.half;
   const int es = div_half(c, hs), et = div_half(c, ht), ps = div_half(c, es), pt = div_half(c, et);
-  const int us = s.res[hs], ut = s.res[ht];
+  const int us = s.lk[hs], ut = s.lk[ht];
   if (es == et) {
     links[0] = hs; links[1] = ht; *nl = 2;
     return imin(us, ut);
@@ -687,8 +815,9 @@ static __device__ int widest_path_warp(const Sm& s, int hs, int ht, int* links, 
   const int ncand = same_pod ? half : half * half;
   for (int i = lane; i < ncand; i += 32) {
     const int a = same_pod ? i : div_half(c, i), cc = same_pod ? 0 : i - a * half;
-    int b = imin(imin(us, ut), imin(s.res[l_ea(c, es, a)], s.res[l_ea(c, et, a)]));
-    if (!same_pod) b = imin(b, imin(s.res[l_ac(c, ps, a, cc)], s.res[l_ac(c, pt, a, cc)]));
+    int b = imin(imin(us, ut), imin(s.lk[s_ea(c, es, a)], s.lk[s_ea(c, et, a)]));
+    if (!same_pod)
+      b = imin(b, imin(s.lk[s_ac(c, ps * half + a, cc)], s.lk[s_ac(c, pt * half + a, cc)]));
     best = path_combine(best, PathSel{b, i});
   }
   for (int o = 16; o > 0; o >>= 1) {
@@ -707,9 +836,10 @@ static __device__ int widest_path_warp(const Sm& s, int hs, int ht, int* links, 
   return best.b;
 }
 
-// a7/a8: commit of pod g on c.winner (warp 0).  Sets c.commit_ok.
+// a7/a8: commit of pod g on c.winner (warp 0).  Sets c.commit_ok; on
+// success also clears the pod's bookkeeping and sets up pod g + 1.
 template <int B>
-static __device__ void commit_warp(const Sm& s, const InstDev& I, int g) {
+static __device__ void commit_warp(const Sm& s, const InstDev& I, int g, Pre& nxt) {
   Ctx& c = *s.c;
   const int lane = lane_id();
   const int u = c.winner;
@@ -733,7 +863,7 @@ static __device__ void commit_warp(const Sm& s, const InstDev& I, int g) {
   bool ok = true;
   for (int base = 0; base < c.npe && ok; base += 32) {
     int4 mine = make_int4(0, 0, 0, 0);
-    if (base + lane < c.npe) mine = c.scr_pe[base + lane];
+    if (base + lane < c.npe) mine = c.pel[base + lane];
     const int cnt = imin(32, c.npe - base);
     for (int i = 0; i < cnt; ++i) {
       const int ew = __shfl_sync(0xffffffffu, mine.x, i);
@@ -756,7 +886,7 @@ static __device__ void commit_warp(const Sm& s, const InstDev& I, int g) {
         const int amount = b >= bmax ? bmax : bmin;
         if (lane == 0) {
           for (int j = 0; j < nl; ++j) {
-            s.res[links[j]] -= amount;
+            s.lk[lslot(c, links[j])] -= amount;
             path[j] = links[j];
           }
           I.o_bw[c.e_off + e] = amount;
@@ -769,12 +899,12 @@ static __device__ void commit_warp(const Sm& s, const InstDev& I, int g) {
   if (!ok) {
     // undo this pod's reservations (links committed before the failure)
     for (int i = lane; i < done; i += 32) {
-      const int e = c.scr_pe[i].x & kLinkIndex;
+      const int e = c.pel[i].x & kLinkIndex;
       int32_t* path = I.o_path + (c.e_off + e) * 6;
       const int bw = I.o_bw[c.e_off + e];
       for (int j = 0; j < 6; ++j) {
         const int l = path[j];
-        if (l >= 0) atomicAdd(&s.res[l], bw);
+        if (l >= 0) atomicAdd(&s.lk[lslot(c, l)], bw);
         path[j] = -1;
       }
       I.o_bw[c.e_off + e] = 0;
@@ -782,8 +912,10 @@ static __device__ void commit_warp(const Sm& s, const InstDev& I, int g) {
     __syncwarp();
     if (lane == 0) {
       atomicOr(&s.trymask[u % B], 1u << (u / B));
+      c.nfail += 1;
       c.commit_ok = 0;
     }
+    __syncwarp();
     return;
   }
   // capacity (Eqs. 4, 6): per resource c^max for every container when the
@@ -794,7 +926,7 @@ static __device__ void commit_warp(const Sm& s, const InstDev& I, int g) {
   const int32_t c0 = c.pc[g], c1 = c.pc[g + 1];
   uint32_t used_c = 0, used_m = 0;
   for (int pos = c0 + lane; pos < c1; pos += 32) {
-    const int4 q = I.c_lay[c.c_off + pos];
+    const int4 q = pos - c0 < 32 ? s.curc[lane] : I.c_lay[c.c_off + pos];
     const int a = take_cpu_max ? ((unsigned)q.y >> 16) : (q.y & 0xffff);
     const int m = take_mem_max ? ((unsigned)q.z >> 16) : (q.z & 0xffff);
     I.o_host[c.c_off + q.x] = u;
@@ -809,8 +941,12 @@ static __device__ void commit_warp(const Sm& s, const InstDev& I, int g) {
   if (lane == 0) {
     s.cm[u] = cm - (used_c | (used_m << 16));
     s.ctr[u] += c.size;
-    c.commit_ok = 1;
   }
+  __syncwarp();
+  pod_clear_warp<B>(s);
+  __syncwarp();
+  if (g + 1 < c.n_p) pod_setup_warp<B>(s, I, g + 1, nxt);
+  if (lane == 0) c.commit_ok = 1;
   __syncwarp();
 }
 
@@ -819,6 +955,7 @@ static __device__ void commit_warp(const Sm& s, const InstDev& I, int g) {
 template <int B>
 static __device__ void give_back(const Sm& s, const InstDev& I, int64_t c_off, int n_c,
                                  int64_t e_off, int n_e, bool clear) {
+  const Ctx& c = *s.c;
   const int tid = threadIdx.x;
   for (int i = tid; i < n_c; i += B) {
     const int h = I.o_host[c_off + i];
@@ -838,30 +975,13 @@ static __device__ void give_back(const Sm& s, const InstDev& I, int64_t c_off, i
     for (int j = 0; j < 6; ++j) {
       const int l = path[j];
       if (l >= 0) {
-        atomicAdd(&s.res[l], bw);
+        atomicAdd(&s.lk[lslot(c, l)], bw);
         if (clear) path[j] = -1;
       }
     }
     if (clear) I.o_bw[e_off + e] = 0;
   }
   __syncthreads();
-}
-
-// Per-pod table reset (block-wide, before setup).
-template <int B>
-static __device__ void reset_tables(const Sm& s) {
-  const Ctx& c = *s.c;
-  const int tid = threadIdx.x;
-  for (int e = tid; e < c.E; e += B) {
-    s.Be[e] = 0;
-    s.T1[e] = kInf; s.T1h[e] = -1; s.T2[e] = kInf;
-    s.S1[e] = kInf; s.S1h[e] = -1; s.S2[e] = kInf;
-  }
-  for (int p = tid; p < c.k; p += B) s.Cp[p] = 0;
-  for (int h = tid; h < kHash; h += B) {
-    s.hkey[h] = -1;
-    s.hcnt[h] = 0;
-  }
 }
 
 template <int B>
@@ -871,8 +991,14 @@ static __device__ void load_instance(const Sm& s, const InstDev& I) {
   if (tid == 0) {
     c.k = I.k; c.half = I.half; c.H = I.H; c.E = I.E; c.C = I.C; c.method = I.method;
     c.link_mbps = I.link_mbps;
+    int gs = 1;
+    while (gs < I.half) gs <<= 1;
+    c.gs = gs;
+    c.ld = I.E + 1;
+    c.ea0 = I.H;
+    c.ac0 = I.H + I.half * c.ld;
     c.mh = ((1ull << 32) + (unsigned long long)I.half - 1) / (unsigned long long)I.half;
-    c.scr_pe = I.scr_pe;
+    c.arrive = 0;
     for (int v = 0; v < kMaxC; ++v) {
       c.W[v] = v < I.C ? I.W[v] : 0.0;
       c.L1[v] = v < I.C ? I.L1[v] : 0.0;
@@ -880,11 +1006,19 @@ static __device__ void load_instance(const Sm& s, const InstDev& I) {
       c.L1f[v] = (float)c.L1[v];
     }
   }
+  __syncthreads();
   for (int u = tid; u < I.H; u += B) {
     s.cm[u] = (uint32_t)I.cpu[u] | ((uint32_t)I.mem[u] << 16);
     s.ctr[u] = I.ctr[u] | (I.pre[u] ? kPreBit : 0);
   }
-  for (int l = tid; l < 3 * I.H; l += B) s.res[l] = I.res[l];
+  for (int l = tid; l < 3 * I.H; l += B) s.lk[lslot(c, l)] = I.res[l];
+  for (int e = tid; e < I.E; e += B) s.Be[e] = 0;
+  for (int p = tid; p < I.k; p += B) s.Cp[p] = 0;
+  for (int h = tid; h < kHash; h += B) {
+    s.hkey[h] = -1;
+    s.hcnt[h] = 0;
+    s.hsum[h] = 0;
+  }
   s.tmark[tid] = 0;
   s.trymask[tid] = 0;
   __syncthreads();
@@ -892,6 +1026,7 @@ static __device__ void load_instance(const Sm& s, const InstDev& I) {
 
 template <int B>
 static __device__ void store_instance(const Sm& s, const InstDev& I) {
+  const Ctx& c = *s.c;
   const int tid = threadIdx.x;
   for (int u = tid; u < I.H; u += B) {
     const uint32_t cm = s.cm[u];
@@ -899,7 +1034,7 @@ static __device__ void store_instance(const Sm& s, const InstDev& I) {
     I.mem[u] = (int32_t)(cm >> 16);
     I.ctr[u] = s.ctr[u] & kCtrMask;
   }
-  for (int l = tid; l < 3 * I.H; l += B) I.res[l] = s.res[l];
+  for (int l = tid; l < 3 * I.H; l += B) I.res[l] = s.lk[lslot(c, l)];
 }
 
 // Request header, and its index arrays staged in shared memory when they
@@ -909,7 +1044,7 @@ static __device__ void load_request(const Sm& s, const InstDev& I, int r, const 
   Ctx& c = *s.c;
   const int tid = threadIdx.x;
   const ReqRec q = I.reqs[r];
-  const bool stage_p = q.n_p + 1 <= kStageP + 1;
+  const bool stage_p = q.n_p <= kStageP;
   const bool stage_c = q.n_c <= kStageC;
   if (tid == 0) {
     c.c_off = q.c_off; c.e_off = q.e_off; c.p_off = q.p_off; c.l_off = q.l_off;
@@ -917,8 +1052,10 @@ static __device__ void load_request(const Sm& s, const InstDev& I, int r, const 
     c.pc = stage_p ? s.st_pc : I.p_coff + q.l_off;
     c.pe = stage_p ? s.st_pe : I.p_eoff + q.l_off;
     c.hof = stage_c ? s.st_hof : I.o_host + q.c_off;
+    c.pel = q.max_pe <= kPeS ? s.pel : I.scr_pe;
+    c.npe = 0;
+    c.nfail = 0;
     c.ndec = 0;
-    c.placed = 0;
   }
   if (stage_p)
     for (int i = tid; i <= q.n_p; i += B) {
@@ -930,37 +1067,30 @@ static __device__ void load_request(const Sm& s, const InstDev& I, int r, const 
   __syncthreads();
 }
 
-// One pod decision (a1..a8).  Returns true when the pod is placed.
+// One pod decision (a2..a8); pod g was set up by warp 0 before.  Returns
+// true when the pod is placed (then pod g + 1 is set up).
 template <int B, int HPT>
-static __device__ bool decide_pod(const Sm& s, const InstDev& I, int g) {
+static __device__ bool decide_pod(const Sm& s, const InstDev& I, int g, Pre& nxt) {
   Ctx& c = *s.c;
   const int tid = threadIdx.x;
-  reset_tables<B>(s);
-  __syncthreads();
-  if (tid < 32) pod_setup_warp(s, I, g);
-  __syncthreads();
-  if (c.npe > 0) {
-    mark_peers<B>(s);
-    build_tables<B>(s);  // starts and ends with a barrier
-  }
+  if (c.npe > 0) build_tables<B>(s);  // ends with a barrier
   column_stats<B>(s);
-  float sc[HPT];
-  score_pass<B, HPT>(s, sc);
   bool placed = false;
   for (;;) {
-    pick_host<B, HPT>(s, sc);
+    pick_host<B>(s);
     if (c.winner < 0) break;
-    if (tid < 32) commit_warp<B>(s, I, g);
+    if (tid < 32) commit_warp<B>(s, I, g, nxt);
     __syncthreads();
     if (c.commit_ok) {
       placed = true;
       break;
     }
   }
-  s.tmark[tid] = 0;
-  s.trymask[tid] = 0;
   if (tid == 0) c.ndec += 1;
-  __syncthreads();
+  if (!placed) {
+    if (tid < 32) pod_clear_warp<B>(s);
+    __syncthreads();
+  }
   return placed;
 }
 
@@ -999,10 +1129,15 @@ static __device__ void schedule_request(const Sm& s, const InstDev& I, int r) {
     for (int j = 0; j < 6; ++j) I.o_path[(e_off + e) * 6 + j] = -1;
   }
   for (int p = tid; p < n_p; p += B) I.o_score[p_off + p] = -1.0;
+  Pre nxt = {make_int4(0, 0, 0, 0), make_int4(0, 0, 0, 0)};
+  if (tid < 32 && n_p > 0) {
+    nxt = prefetch_pod(c, I, 0);
+    pod_setup_warp<B>(s, I, 0, nxt);
+  }
   __syncthreads();
   int g = 0;
   for (; g < n_p; ++g)
-    if (!decide_pod<B, HPT>(s, I, g)) break;
+    if (!decide_pod<B, HPT>(s, I, g, nxt)) break;
   const bool accepted = g == n_p;
   if (accepted) {
     // links inside a pod use no network link and get bw^max
@@ -1014,9 +1149,11 @@ static __device__ void schedule_request(const Sm& s, const InstDev& I, int r) {
     give_back<B>(s, I, c_off, n_c, e_off, n_e, true);
   }
   pod_scores<B>(s, I, g);
+  __syncthreads();
   if (tid == 0) {
     I.o_status[r] = accepted ? DC_ACCEPTED : DC_REJECTED;
     I.o_ndec[r] = c.ndec;
+    I.o_tdone[r] = (long long)globaltimer_ns();
     atomicAdd(&I.counters[0], (unsigned long long)c.ndec);
     atomicAdd(&I.counters[1], (unsigned long long)c.ndec * (unsigned long long)c.H);
   }
@@ -1028,6 +1165,7 @@ __global__ void __launch_bounds__(B, 1) k_schedule(const InstDev* __restrict__ i
   extern __shared__ __align__(16) unsigned char smem[];
   const InstDev& I = insts[blockIdx.x];
   const Sm s = carve(smem, I.k, B);
+  if (threadIdx.x == 0) atomicMin(&I.counters[2], globaltimer_ns());
   load_instance<B>(s, I);
   for (int op = 0; op < I.n_ops; ++op) {
     const int w = I.ops[op];
@@ -1064,14 +1202,12 @@ __global__ void __launch_bounds__(B, 1) k_rank(const InstDev* __restrict__ inst,
     if (threadIdx.x == 0) s.c->hof = const_cast<int32_t*>(host_of);
     __syncthreads();
   }
-  reset_tables<B>(s);
-  __syncthreads();
-  if (threadIdx.x < 32) pod_setup_warp(s, I, g);
-  __syncthreads();
-  if (s.c->npe > 0) {
-    mark_peers<B>(s);
-    build_tables<B>(s);
+  if (threadIdx.x < 32) {
+    Pre p = prefetch_pod(*s.c, I, g);
+    pod_setup_warp<B>(s, I, g, p);
   }
+  __syncthreads();
+  if (s.c->npe > 0) build_tables<B>(s);
   column_stats<B>(s);
   column_fp64<B>(s);
   const Ctx& c = *s.c;
@@ -1079,7 +1215,7 @@ __global__ void __launch_bounds__(B, 1) k_rank(const InstDev* __restrict__ inst,
     int32_t x[kMaxC];
     const bool f = host_crit<B>(s, u, x);
     feas[u] = f ? 1 : 0;
-    s32[u] = f ? score32(c, x) : __int_as_float(0x7fc00000);
+    s32[u] = f ? closeness32(c, x) : __int_as_float(0x7fc00000);
     s64[u] = f ? score64(c.method, c.C, c.W, c.L1, c.norm, c.Ap, c.An, c.Td, x)
                : __longlong_as_double(0x7ff8000000000000ll);
     for (int v = 0; v < c.C; ++v) crit[(int64_t)u * c.C + v] = x[v];

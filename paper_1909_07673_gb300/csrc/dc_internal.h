@@ -27,8 +27,8 @@ constexpr int32_t kOpRelease = 1 << 30;
 constexpr int32_t kPeSrc = 1 << 30;
 constexpr int32_t kMaxLinksPerRequest = 1 << 18;
 constexpr int32_t kMaxK = 32;
-constexpr int kChunk = 6;    // peer links per table-building chunk
-constexpr int kHash = 1024;  // slots of the per-pod peer-host hash table
+constexpr int kHash = 256;   // slots of the per-pod peer-host hash table
+constexpr int kPeS = 256;    // peer links of one pod kept in shared memory
 constexpr int kMaxBlock = 1024;
 
 // Link-record flags (e_lay[].x): the link joins two containers of one pod;
@@ -48,7 +48,8 @@ constexpr int kStageC = 1024;  // containers
 // / e_off; pod scores from p_off.
 struct ReqRec {
   int64_t c_off, e_off, p_off, l_off;
-  int32_t n_c, n_e, n_p, pad;
+  int32_t n_c, n_e, n_p;
+  int32_t max_pe;  // most links from one pod to earlier pods
 };
 
 // Per-pod decision record kept for the FP64 score of the chosen host: its
@@ -78,6 +79,7 @@ struct InstDev {
   const int32_t *p_coff, *p_eoff;
   int32_t *o_host, *o_cpu, *o_mem, *o_bw, *o_path, *o_status, *o_ndec;
   double* o_score;
+  long long* o_tdone;  // [requests] device clock (ns) at completion
   // operations of this launch, FCFS
   const int32_t* ops;
   int32_t n_ops;
@@ -86,39 +88,51 @@ struct InstDev {
   int4* scr_pe;       // peer links of the pod being placed
   PodLog* scr_log;    // [pods of the current request]
   int32_t* err;       // [1] 0 or a DC_E_* code
-  unsigned long long* counters;  // [2] pod decisions, host rankings (accumulated)
+  // [3] pod decisions, host rankings (accumulated), launch start clock (min)
+  unsigned long long* counters;
 };
 
 DC_HD inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Shared-memory layout of one scheduling block (bytes), see dc_kernels.cu.
 struct SmemLayout {
-  size_t ctx, cm, ctr, res, tab, cp, g, tmark, trymask, hkey, hcnt, red64, red32, sel;
-  size_t st_pc, st_pe, st_hof, total;
+  size_t ctx, cm, ctr, lk, tab, cp, tmark, trymask, hkey, hcnt, hsum, red64, red32, sel;
+  size_t st_pc, st_pe, st_hof, pel, curc, total;
 };
+
+// Link residuals in shared memory: host links [0, H), then edge-aggregation
+// links transposed as [a][E + 1], then aggregation-core links as
+// [c][E + 1] (E = k^2/2 edge = aggregation switches; the padding keeps
+// threads over consecutive switches on distinct banks).
+DC_HD inline size_t link_slots(int k) {
+  const size_t H = (size_t)k * k * k / 4, E = (size_t)k * k / 2, half = (size_t)k / 2;
+  return H + 2 * half * (E + 1);
+}
 
 DC_HD inline SmemLayout smem_layout(int k, int block, size_t ctx_bytes) {
   SmemLayout L;
-  const size_t H = (size_t)k * k * k / 4, E = (size_t)k * k / 2, half = (size_t)k / 2;
+  const size_t H = (size_t)k * k * k / 4, E = (size_t)k * k / 2;
   const size_t nw = (size_t)block / 32;
   size_t o = 0;
   L.ctx = o; o = align_up(o + ctx_bytes, 16);
   L.cm = o; o = align_up(o + 4 * H, 16);
   L.ctr = o; o = align_up(o + 4 * H, 16);
-  L.res = o; o = align_up(o + 12 * H, 16);
+  L.lk = o; o = align_up(o + 4 * link_slots(k), 16);
   L.tab = o; o = align_up(o + 7 * 4 * E, 16);
   L.cp = o; o = align_up(o + 4 * (size_t)k, 16);
-  L.g = o; o = align_up(o + 4 * (size_t)kChunk * k * half, 16);
   L.tmark = o; o = align_up(o + 4 * (size_t)block, 16);
   L.trymask = o; o = align_up(o + 4 * (size_t)block, 16);
   L.hkey = o; o = align_up(o + 4 * (size_t)kHash, 16);
   L.hcnt = o; o = align_up(o + 4 * (size_t)kHash, 16);
+  L.hsum = o; o = align_up(o + 8 * (size_t)kHash, 16);
   L.red64 = o; o = align_up(o + 8 * nw * 2 * kMaxC, 16);
   L.red32 = o; o = align_up(o + 4 * nw * (2 * kMaxC + 1), 16);
   L.sel = o; o = align_up(o + 16 * nw, 16);
   L.st_pc = o; o = align_up(o + 4 * (size_t)(kStageP + 1), 16);
   L.st_pe = o; o = align_up(o + 4 * (size_t)(kStageP + 1), 16);
   L.st_hof = o; o = align_up(o + 4 * (size_t)kStageC, 16);
+  L.pel = o; o = align_up(o + 16 * (size_t)kPeS, 16);
+  L.curc = o; o = align_up(o + 16 * 32, 16);
   L.total = o;
   return L;
 }

@@ -97,10 +97,9 @@ int pick_block(int k) {
     const int H = k * k * k / 4;
     if (max_hosts_per_thread(b) > 0 && H <= b * max_hosts_per_thread(b)) return b;
   }
+  // measured on GB300 (one block per data center): 512 threads for k >= 16
   if (k <= 4) return 128;
   if (k <= 8) return 256;
-  if (k <= 16) return 1024;
-  if (k <= 24) return 512;
   return 512;
 }
 
@@ -149,8 +148,11 @@ struct dc_t {
   // device outputs and their pinned host mirror
   DevVec<int32_t> o_host, o_cpu, o_mem, o_bw, o_path, o_status, o_ndec;
   DevVec<double> o_score;
+  DevVec<long long> o_tdone;
   PinnedVec<int32_t> m_host, m_cpu, m_mem, m_bw, m_path, m_status, m_ndec;
   PinnedVec<double> m_score;
+  PinnedVec<long long> m_tdone;
+  int64_t h2d_bytes = 0, d2h_bytes = 0;
   DevVec<int4> d_scr_pe;
   DevVec<PodLog> d_scr_log;
   int32_t scr_links = 0, scr_pods = 0;
@@ -180,7 +182,7 @@ struct dc_plan {
   InstDev* d_desc = nullptr;
   int32_t* d_ops = nullptr;
   unsigned long long* d_counters = nullptr;
-  unsigned long long h_counters[2] = {0, 0};
+  unsigned long long h_counters[3] = {0, 0, 0};
   std::vector<cudaStream_t> side;
   std::vector<cudaEvent_t> fork_ev, join_ev;
   cudaEvent_t done_ev = nullptr;
@@ -244,7 +246,7 @@ int store_request(dc_t* d, const dc_request* q) {
     if (q->mem_min[i] < 0 || q->mem_min[i] > q->mem_max[i] || q->mem_max[i] > 65535) return DC_E_INVAL;
     P = std::max(P, q->pod[i] + 1);
   }
-  std::vector<int32_t> pc(P + 1, 0), pe(P + 1, 0);
+  std::vector<int32_t> pc(P + 1, 0), pe(P + 1, 0), npeer(P, 0);
   for (int32_t i = 0; i < n; ++i) pc[q->pod[i] + 1] += 1;
   for (int32_t g = 0; g < P; ++g)
     if (pc[g + 1] == 0) return DC_E_INVAL;  // pod ids must be dense
@@ -252,8 +254,12 @@ int store_request(dc_t* d, const dc_request* q) {
     if (q->src[e] < 0 || q->src[e] >= n || q->dst[e] < 0 || q->dst[e] >= n) return DC_E_INVAL;
     if (q->src[e] == q->dst[e]) return DC_E_INVAL;
     if (q->bw_min[e] < 0 || q->bw_min[e] > q->bw_max[e]) return DC_E_INVAL;
-    pe[std::max(q->pod[q->src[e]], q->pod[q->dst[e]]) + 1] += 1;
+    const int32_t later = std::max(q->pod[q->src[e]], q->pod[q->dst[e]]);
+    pe[later + 1] += 1;
+    if (q->pod[q->src[e]] != q->pod[q->dst[e]]) npeer[later] += 1;
   }
+  int32_t max_pe = 0;
+  for (int32_t g = 0; g < P; ++g) max_pe = std::max(max_pe, npeer[g]);
   for (int32_t g = 0; g < P; ++g) {
     pc[g + 1] += pc[g];
     pe[g + 1] += pe[g];
@@ -289,6 +295,7 @@ int store_request(dc_t* d, const dc_request* q) {
   r.n_c = n;
   r.n_e = m;
   r.n_p = P;
+  r.max_pe = max_pe;
   DC_TRY(d->reqs.append(&r, 1));
   d->tot_c += n;
   d->tot_e += m;
@@ -321,6 +328,7 @@ int stage(dc_t* d) {
   DC_TRY(d->o_score.ensure(d->tot_p, done_p, st));
   DC_TRY(d->o_status.ensure(R, d->staged, st));
   DC_TRY(d->o_ndec.ensure(R, d->staged, st));
+  DC_TRY(d->o_tdone.ensure(R, d->staged, st));
   if (d->max_links > d->scr_links || !d->d_scr_pe.p) {
     DC_TRY(d->d_scr_pe.ensure(std::max<size_t>(1, d->max_links), 0, st));
     d->scr_links = (int32_t)d->d_scr_pe.cap;
@@ -340,6 +348,8 @@ int stage(dc_t* d) {
     }
     DC_CUDA(cudaMemcpyAsync(d->d_reqs.p + d->staged, d->reqs.p + d->staged,
                             (R - d->staged) * sizeof(ReqRec), cudaMemcpyHostToDevice, st));
+    d->h2d_bytes += (nc + ne) * (int64_t)sizeof(int4) + 2 * nl * 4 +
+                    (int64_t)(R - d->staged) * (int64_t)sizeof(ReqRec);
     d->staged = R;
     d->st_c = d->tot_c;
     d->st_e = d->tot_e;
@@ -353,6 +363,7 @@ int stage(dc_t* d) {
   DC_TRY(d->m_score.resize(d->tot_p));
   DC_TRY(d->m_status.resize(R));
   DC_TRY(d->m_ndec.resize(R));
+  DC_TRY(d->m_tdone.resize(R));
   return DC_OK;
 }
 
@@ -375,6 +386,7 @@ InstDev make_desc(dc_t* d, const int32_t* d_ops, int n_ops, unsigned long long* 
   I.o_host = d->o_host.p; I.o_cpu = d->o_cpu.p; I.o_mem = d->o_mem.p;
   I.o_bw = d->o_bw.p; I.o_path = d->o_path.p; I.o_status = d->o_status.p; I.o_ndec = d->o_ndec.p;
   I.o_score = d->o_score.p;
+  I.o_tdone = d->o_tdone.p;
   I.ops = d_ops;
   I.n_ops = n_ops;
   I.scr_links = d->scr_links;
@@ -394,6 +406,7 @@ int enqueue_plan(dc_plan* p, cudaStream_t st) {
       DC_CUDA(cudaMemcpyAsync(d->d_state, d->d_init, sizeof(int32_t) * 7 * (size_t)d->H,
                               cudaMemcpyDeviceToDevice, st));
   DC_CUDA(cudaMemsetAsync(p->d_counters, 0, 2 * sizeof(unsigned long long), st));
+  DC_CUDA(cudaMemsetAsync(p->d_counters + 2, 0xff, sizeof(unsigned long long), st));
   const size_t G = p->groups.size();
   if (G == 1) {
     const auto& g = p->groups[0];
@@ -448,6 +461,9 @@ int enqueue_collect(dc_plan* p, cudaStream_t st) {
     if (p1 > p0)
       DC_CUDA(cudaMemcpyAsync(d->m_score.p + p0, d->o_score.p + p0, (p1 - p0) * 8, cudaMemcpyDeviceToHost, st));
     DC_CUDA(cudaMemcpyAsync(d->m_ndec.p + r0, d->o_ndec.p + r0, (r1 - r0) * 4, cudaMemcpyDeviceToHost, st));
+    DC_CUDA(cudaMemcpyAsync(d->m_tdone.p + r0, d->o_tdone.p + r0, (r1 - r0) * 8, cudaMemcpyDeviceToHost, st));
+    d->d2h_bytes += (c1 - c0) * 12 + (e1 - e0) * 28 + (p1 - p0) * 8 + (int64_t)(r1 - r0) * 12 +
+                    (int64_t)d->reqs.n * 4;
   }
   return DC_OK;
 }
@@ -551,6 +567,7 @@ void dc_destroy(dc_t* d) {
   d->d_reqs.release(st);
   d->o_host.release(st); d->o_cpu.release(st); d->o_mem.release(st); d->o_bw.release(st);
   d->o_path.release(st); d->o_status.release(st); d->o_ndec.release(st); d->o_score.release(st);
+  d->o_tdone.release(st);
   d->d_scr_pe.release(st);
   d->d_scr_log.release(st);
   cudaStreamSynchronize(st);
@@ -558,6 +575,7 @@ void dc_destroy(dc_t* d) {
   d->reqs.release();
   d->m_host.release(); d->m_cpu.release(); d->m_mem.release(); d->m_bw.release();
   d->m_path.release(); d->m_status.release(); d->m_ndec.release(); d->m_score.release();
+  d->m_tdone.release();
   if (d->d_state) cudaFree(d->d_state);
   if (d->d_init) cudaFree(d->d_init);
   if (d->d_W) cudaFree(d->d_W);
@@ -576,6 +594,12 @@ int dc_submit_request(dc_t* d, const dc_request* q, int64_t* req_id) {
   d->release_queued.push_back(0);
   d->gen += 1;
   if (req_id) *req_id = (int64_t)r;
+  return DC_OK;
+}
+
+int dc_submit_batch(dc_t* d, int32_t n, const dc_request* reqs, int64_t* req_ids) {
+  if (!d || n < 0 || (n > 0 && !reqs)) return DC_E_INVAL;
+  for (int32_t i = 0; i < n; ++i) DC_TRY(dc_submit_request(d, reqs + i, req_ids ? req_ids + i : nullptr));
   return DC_OK;
 }
 
@@ -639,7 +663,7 @@ int dc_plan_create(dc_t* const* dcs, int32_t n, int32_t flags, dc_plan** out) {
     const size_t n_ops_total = std::max<size_t>(1, all_ops.size());
     if (cudaMallocAsync((void**)&p->d_ops, n_ops_total * 4, p->home) != cudaSuccess ||
         cudaMallocAsync((void**)&p->d_desc, n * sizeof(InstDev), p->home) != cudaSuccess ||
-        cudaMallocAsync((void**)&p->d_counters, 2 * sizeof(unsigned long long), p->home) !=
+        cudaMallocAsync((void**)&p->d_counters, 3 * sizeof(unsigned long long), p->home) !=
             cudaSuccess)
       rc = DC_E_NOMEM;
     if (rc == DC_OK && !all_ops.empty())
@@ -736,7 +760,7 @@ int dc_plan_collect(dc_plan* p) {
   DC_CUDA(cudaStreamWaitEvent(p->home, p->done_ev, 0));
   DC_TRY(enqueue_collect(p, p->home));
   DC_CUDA(cudaStreamSynchronize(p->home));
-  DC_CUDA(cudaMemcpy(p->h_counters, p->d_counters, 2 * sizeof(unsigned long long),
+  DC_CUDA(cudaMemcpy(p->h_counters, p->d_counters, 3 * sizeof(unsigned long long),
                      cudaMemcpyDeviceToHost));
   int32_t err = 0;
   for (dc_t* d : p->dcs) {
@@ -752,11 +776,20 @@ int dc_plan_collect(dc_plan* p) {
   return DC_OK;
 }
 
-int dc_plan_stats(dc_plan* p, int64_t* decisions, int64_t* host_rankings, int32_t* kernels) {
+int dc_plan_stats(dc_plan* p, int64_t* decisions, int64_t* host_rankings, int32_t* kernels,
+                  int64_t* start_ns) {
   if (!p) return DC_E_INVAL;
   if (decisions) *decisions = (int64_t)p->h_counters[0];
   if (host_rankings) *host_rankings = (int64_t)p->h_counters[1];
   if (kernels) *kernels = (int32_t)p->groups.size();
+  if (start_ns) *start_ns = (int64_t)p->h_counters[2];
+  return DC_OK;
+}
+
+int dc_io_stats(dc_t* d, int64_t* h2d, int64_t* d2h) {
+  if (!d) return DC_E_INVAL;
+  if (h2d) *h2d = d->h2d_bytes;
+  if (d2h) *d2h = d->d2h_bytes;
   return DC_OK;
 }
 
@@ -829,6 +862,7 @@ int dc_query(dc_t* d, int64_t req_id, dc_result* out, int32_t wait) {
   if (out->bw) std::memcpy(out->bw, d->m_bw.p + q.e_off, q.n_e * 4);
   if (out->path) std::memcpy(out->path, d->m_path.p + 6 * q.e_off, (size_t)q.n_e * 24);
   if (out->pod_score) std::memcpy(out->pod_score, d->m_score.p + q.p_off, q.n_p * 8);
+  out->done_ns = d->m_tdone.p[req_id];
   return DC_OK;
 }
 
@@ -928,12 +962,14 @@ int dc_rank_hosts(dc_t* d, const dc_request* q, int32_t pod, const int32_t* host
   tmp.d_reqs.release(st);
   tmp.o_host.release(st); tmp.o_cpu.release(st); tmp.o_mem.release(st); tmp.o_bw.release(st);
   tmp.o_path.release(st); tmp.o_status.release(st); tmp.o_ndec.release(st); tmp.o_score.release(st);
+  tmp.o_tdone.release(st);
   tmp.d_scr_pe.release(st);
   tmp.d_scr_log.release(st);
   tmp.c_lay.release(); tmp.e_lay.release(); tmp.p_coff.release(); tmp.p_eoff.release();
   tmp.reqs.release();
   tmp.m_host.release(); tmp.m_cpu.release(); tmp.m_mem.release(); tmp.m_bw.release();
   tmp.m_path.release(); tmp.m_status.release(); tmp.m_ndec.release(); tmp.m_score.release();
+  tmp.m_tdone.release();
   cudaStreamSynchronize(st);
   tmp.d_state = nullptr; tmp.d_L1 = nullptr; tmp.d_err = nullptr;
   return rc == DC_OK ? nviable : rc;

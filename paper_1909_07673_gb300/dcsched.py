@@ -51,7 +51,7 @@ class _Request(C.Structure):
 class _Result(C.Structure):
     _fields_ = [("status", C.c_int32), ("n_decisions", C.c_int32), ("host", _i32p),
                 ("cpu", _i32p), ("mem", _i32p), ("bw", _i32p), ("path", _i32p),
-                ("pod_score", _f64p)]
+                ("pod_score", _f64p), ("done_ns", C.c_int64)]
 
 
 _lib = None
@@ -71,6 +71,8 @@ def lib():
         L.dc_destroy.argtypes = [C.c_void_p]
         L.dc_destroy.restype = None
         L.dc_submit_request.argtypes = [C.c_void_p, C.POINTER(_Request), _i64p]
+        L.dc_submit_batch.argtypes = [C.c_void_p, C.c_int32, C.POINTER(_Request), _i64p]
+        L.dc_io_stats.argtypes = [C.c_void_p, _i64p, _i64p]
         L.dc_release.argtypes = [C.c_void_p, C.c_int64]
         L.dc_schedule.argtypes = [C.POINTER(C.c_void_p), C.c_int32, C.c_int32]
         L.dc_query.argtypes = [C.c_void_p, C.c_int64, C.POINTER(_Result), C.c_int32]
@@ -82,7 +84,7 @@ def lib():
                                      C.POINTER(C.c_void_p)]
         L.dc_plan_launch.argtypes = [C.c_void_p, C.c_void_p]
         L.dc_plan_collect.argtypes = [C.c_void_p]
-        L.dc_plan_stats.argtypes = [C.c_void_p, _i64p, _i64p, _i32p]
+        L.dc_plan_stats.argtypes = [C.c_void_p, _i64p, _i64p, _i32p, _i64p]
         L.dc_plan_destroy.argtypes = [C.c_void_p]
         L.dc_plan_destroy.restype = None
         _lib = L
@@ -169,11 +171,33 @@ class DataCenter:
                "mem": np.zeros(n, np.int32), "bw": np.zeros(m, np.int32),
                "path": np.zeros(6 * m, np.int32), "pod_score": np.zeros(P, np.float64)}
         res = _Result(0, 0, *(_p(out[x], _i32p) for x in ("host", "cpu", "mem", "bw", "path")),
-                      _p(out["pod_score"], _f64p))
+                      _p(out["pod_score"], _f64p), 0)
         _check(lib().dc_query(self.h, req_id, C.byref(res), 1 if wait else 0), "dc_query")
         out["status"] = int(res.status)
         out["n_decisions"] = int(res.n_decisions)
+        out["done_ns"] = int(res.done_ns)
         return out
+
+    def status(self, req_id: int, wait: bool = True):
+        """(status, n_decisions, done_ns) without copying the placement."""
+        res = _Result(0, 0, None, None, None, None, None, None, 0)
+        _check(lib().dc_query(self.h, req_id, C.byref(res), 1 if wait else 0), "dc_query")
+        return int(res.status), int(res.n_decisions), int(res.done_ns)
+
+    def submit_batch(self, batch) -> int:
+        """Submits every request of a workloads.RequestBatch in order with one
+        call; returns the id of the first."""
+        reqs = [_Req(batch.request(r)) for r in range(batch.n)]
+        arr = (_Request * len(reqs))(*[r.s for r in reqs])
+        ids = np.zeros(max(1, len(reqs)), np.int64)
+        _check(lib().dc_submit_batch(self.h, len(reqs), arr, _p(ids, _i64p)), "dc_submit_batch")
+        self._reqs.extend(reqs)
+        return int(ids[0])
+
+    def io_stats(self):
+        a, b = C.c_int64(), C.c_int64()
+        _check(lib().dc_io_stats(self.h, C.byref(a), C.byref(b)), "dc_io_stats")
+        return a.value, b.value
 
     def state(self, field: int) -> np.ndarray:
         n = 3 * self.H if field == LINK_RES else self.H
@@ -224,9 +248,11 @@ class Plan:
         _check(lib().dc_plan_collect(self.h), "dc_plan_collect")
 
     def stats(self):
-        d, hr, kc = C.c_int64(), C.c_int64(), C.c_int32()
-        _check(lib().dc_plan_stats(self.h, C.byref(d), C.byref(hr), C.byref(kc)), "dc_plan_stats")
-        return d.value, hr.value, kc.value
+        """(decisions, host rankings, kernels per launch, start clock ns)"""
+        d, hr, kc, t0 = C.c_int64(), C.c_int64(), C.c_int32(), C.c_int64()
+        _check(lib().dc_plan_stats(self.h, C.byref(d), C.byref(hr), C.byref(kc), C.byref(t0)),
+               "dc_plan_stats")
+        return d.value, hr.value, kc.value, t0.value
 
     def close(self):
         if getattr(self, "h", None) and _lib is not None:
@@ -242,7 +268,10 @@ def load_instance(inst, stream=None, max_requests: Optional[int] = None) -> Data
     stream of operations (schedules and releases)."""
     dc = DataCenter.from_instance(inst, stream=stream)
     R = inst.reqs.n if max_requests is None else min(max_requests, inst.reqs.n)
-    ops = inst.ops if inst.ops is not None else [(0, r) for r in range(inst.reqs.n)]
+    if inst.ops is None:
+        dc.submit_batch(inst.reqs if R == inst.reqs.n else inst.reqs.subset(range(R)))
+        return dc
+    ops = inst.ops
     for kind, r in ops:
         if r >= R:
             if kind == 0:

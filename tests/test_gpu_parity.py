@@ -121,7 +121,7 @@ def test_plan_graph_replay(ds, stream):
     for rep in range(3):
         plan.launch(stream)
         plan.collect()
-        dec, hr, nk = plan.stats()
+        dec, hr, nk, t0 = plan.stats()
         assert dec > 0 and hr >= dec * 128 and nk == 2
         now = [[dc.query(r) for r in range(inst.reqs.n)] for dc, inst in zip(dcs, wl.instances)]
         if first is None:
