@@ -172,6 +172,23 @@ int dc_query_state(dc_t* dc, int32_t field, int32_t* out, int64_t len);
 int dc_rank_hosts(dc_t* dc, const dc_request* req, int32_t pod, const int32_t* host_of,
                   int32_t* feasible, float* score32, double* score64, int32_t* crit);
 
+/* dc_rank_hosts without any allocation (the paper has no counterpart; this
+ * serves callers that cannot allocate device memory when they rank, e.g. a
+ * process whose device memory is reserved up front by its own pool, or a
+ * latency-critical path that cannot afford the device-wide synchronization
+ * of cudaFree).  Same arguments, outputs and return value as dc_rank_hosts.
+ * Every device temporary lives in one 1 MiB static device array held by
+ * each GPU that loads the library until the process exits; host-side it
+ * uses thread-local buffers.  Limits (DC_E_INVAL beyond): at most 1024
+ * containers and 4096 links in `req`, k <= 32.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  All
+ * calls share the array, which keeps the last call's contents (every byte a
+ * call reads is written by that call first); calls whose work overlaps on
+ * the GPU race on it.  Blocks until the outputs are copied. */
+int dc_rank_hosts_static(dc_t* dc, const dc_request* req, int32_t pod, const int32_t* host_of,
+                         int32_t* feasible, float* score32, double* score64, int32_t* crit);
+
 /* Restores the state given at dc_create and forgets every request. */
 int dc_reset(dc_t* dc);
 

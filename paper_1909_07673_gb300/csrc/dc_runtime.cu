@@ -976,3 +976,204 @@ int dc_rank_hosts(dc_t* d, const dc_request* q, int32_t pod, const int32_t* host
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of dc_rank_hosts.
+//
+// Some callers cannot allocate device memory at the time they need a ranking:
+// a serving process that reserves all device memory up front for its own
+// pool (a cudaMalloc would fail or fight that pool), or a latency-critical
+// path that keeps other streams busy (cudaFree and growing allocations
+// synchronize the whole device).  dc_rank_hosts_static serves them: every
+// device temporary of the ranking (the request in the kernels' layout, the
+// host_of array, the launch descriptor, the peer-link scratch and the
+// per-host outputs) lives in one file-scope device array of
+// kStaticScratchBytes, which every GPU that loads this library holds until
+// the process exits.  Host-side it uses thread-local fixed-size buffers.
+namespace {
+
+constexpr size_t kStaticScratchBytes = 1u << 20;  // 1 MiB
+constexpr int32_t kStaticMaxContainers = 1024;
+constexpr int32_t kStaticMaxLinks = 4096;
+constexpr int32_t kStaticMaxHosts = 8192;  // k <= 32
+
+struct StaticLayout {
+  size_t desc, req, c_lay, e_lay, pc, pe, hof, pel, log, feas, s32, s64, crit, nv, total;
+};
+constexpr size_t a256(size_t x) { return (x + 255) / 256 * 256; }
+constexpr StaticLayout static_layout() {
+  StaticLayout L{};
+  size_t o = 0;
+  L.desc = o; o = a256(o + sizeof(InstDev));
+  L.req = o; o = a256(o + sizeof(ReqRec));
+  L.c_lay = o; o = a256(o + sizeof(int4) * kStaticMaxContainers);
+  L.e_lay = o; o = a256(o + sizeof(int4) * kStaticMaxLinks);
+  L.pc = o; o = a256(o + 4 * (kStaticMaxContainers + 1));
+  L.pe = o; o = a256(o + 4 * (kStaticMaxContainers + 1));
+  L.hof = o; o = a256(o + 4 * kStaticMaxContainers);
+  L.pel = o; o = a256(o + sizeof(int4) * kStaticMaxLinks);
+  L.log = o; o = a256(o + sizeof(PodLog));
+  L.feas = o; o = a256(o + 4 * kStaticMaxHosts);
+  L.s32 = o; o = a256(o + 4 * kStaticMaxHosts);
+  L.s64 = o; o = a256(o + 8 * kStaticMaxHosts);
+  L.crit = o; o = a256(o + 4 * kMaxC * kStaticMaxHosts);
+  L.nv = o; o = a256(o + 4);
+  L.total = o;
+  return L;
+}
+static_assert(static_layout().total <= kStaticScratchBytes, "static scratch too small");
+
+__device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+// Device address of g_static_scratch per device (the host-side name is only a
+// stand-in for the symbol, never a device address).
+constexpr int kMaxDevices = 64;
+unsigned char* g_static_ptr[kMaxDevices] = {nullptr};
+
+int static_scratch(unsigned char** out) {
+  int dev = 0;
+  DC_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices) return DC_E_INVAL;
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    DC_CUDA(cudaGetSymbolAddress(&p, g_static_scratch));
+    g_static_ptr[dev] = static_cast<unsigned char*>(p);
+  }
+  *out = g_static_ptr[dev];
+  return DC_OK;
+}
+
+// Request in the kernels' layout, built without heap allocation.
+struct StaticReq {
+  int4 c_lay[kStaticMaxContainers];
+  int4 e_lay[kStaticMaxLinks];
+  int32_t pc[kStaticMaxContainers + 1], pe[kStaticMaxContainers + 1];
+  int32_t fc[kStaticMaxContainers + 1], fe[kStaticMaxContainers + 1];
+  int32_t npeer[kStaticMaxContainers];
+};
+thread_local StaticReq t_static_req;
+
+int build_static_request(const dc_request* q, StaticReq* w, ReqRec* rec) {
+  const int32_t n = q->n_containers, m = q->n_edges;
+  if (n < 0 || m < 0) return DC_E_INVAL;
+  if (n > kStaticMaxContainers || m > kStaticMaxLinks) return DC_E_INVAL;
+  if ((n > 0 && (!q->cpu_min || !q->cpu_max || !q->mem_min || !q->mem_max || !q->pod)) ||
+      (m > 0 && (!q->src || !q->dst || !q->bw_min || !q->bw_max)))
+    return DC_E_INVAL;
+  int32_t P = 0;
+  for (int32_t i = 0; i < n; ++i) {
+    if (q->pod[i] < 0 || q->pod[i] >= n) return DC_E_INVAL;
+    if (q->cpu_min[i] < 0 || q->cpu_min[i] > q->cpu_max[i] || q->cpu_max[i] > 65535) return DC_E_INVAL;
+    if (q->mem_min[i] < 0 || q->mem_min[i] > q->mem_max[i] || q->mem_max[i] > 65535) return DC_E_INVAL;
+    P = std::max(P, q->pod[i] + 1);
+  }
+  for (int32_t g = 0; g <= P; ++g) w->pc[g] = w->pe[g] = 0;
+  for (int32_t g = 0; g < P; ++g) w->npeer[g] = 0;
+  for (int32_t i = 0; i < n; ++i) w->pc[q->pod[i] + 1] += 1;
+  for (int32_t g = 0; g < P; ++g)
+    if (w->pc[g + 1] == 0) return DC_E_INVAL;
+  for (int32_t e = 0; e < m; ++e) {
+    if (q->src[e] < 0 || q->src[e] >= n || q->dst[e] < 0 || q->dst[e] >= n) return DC_E_INVAL;
+    if (q->src[e] == q->dst[e]) return DC_E_INVAL;
+    if (q->bw_min[e] < 0 || q->bw_min[e] > q->bw_max[e]) return DC_E_INVAL;
+    const int32_t later = std::max(q->pod[q->src[e]], q->pod[q->dst[e]]);
+    w->pe[later + 1] += 1;
+    if (q->pod[q->src[e]] != q->pod[q->dst[e]]) w->npeer[later] += 1;
+  }
+  int32_t max_pe = 0;
+  for (int32_t g = 0; g < P; ++g) {
+    w->pc[g + 1] += w->pc[g];
+    w->pe[g + 1] += w->pe[g];
+    max_pe = std::max(max_pe, w->npeer[g]);
+  }
+  for (int32_t g = 0; g < P; ++g) {
+    w->fc[g] = w->pc[g];
+    w->fe[g] = w->pe[g];
+  }
+  for (int32_t i = 0; i < n; ++i)
+    w->c_lay[w->fc[q->pod[i]]++] = make_int4(i, q->cpu_min[i] | (q->cpu_max[i] << 16),
+                                             q->mem_min[i] | (q->mem_max[i] << 16), 0);
+  for (int32_t e = 0; e < m; ++e) {
+    const int32_t ps = q->pod[q->src[e]], pt = q->pod[q->dst[e]];
+    int32_t wd = e, other;
+    if (ps == pt) {
+      wd |= kLinkIntra;
+      other = q->dst[e];
+    } else if (ps > pt) {
+      wd |= kLinkMineSrc;
+      other = q->dst[e];
+    } else {
+      other = q->src[e];
+    }
+    w->e_lay[w->fe[std::max(ps, pt)]++] = make_int4(wd, other, q->bw_min[e], q->bw_max[e]);
+  }
+  *rec = ReqRec{};
+  rec->n_c = n;
+  rec->n_e = m;
+  rec->n_p = P;
+  rec->max_pe = max_pe;
+  return DC_OK;
+}
+
+}  // namespace
+
+extern "C" int dc_rank_hosts_static(dc_t* d, const dc_request* q, int32_t pod,
+                                    const int32_t* host_of, int32_t* feasible, float* score32,
+                                    double* score64, int32_t* crit) {
+  if (!d || !q || !host_of) return DC_E_INVAL;
+  if (d->H > kStaticMaxHosts) return DC_E_INVAL;
+  StaticReq* w = &t_static_req;
+  ReqRec rec;
+  DC_TRY(build_static_request(q, w, &rec));
+  if (pod < 0 || pod >= rec.n_p) return DC_E_INVAL;
+  for (int32_t i = 0; i < rec.n_c; ++i) {
+    if (q->pod[i] < pod && (host_of[i] < 0 || host_of[i] >= d->H)) return DC_E_INVAL;
+  }
+  unsigned char* base = nullptr;
+  DC_TRY(static_scratch(&base));
+  constexpr StaticLayout L = static_layout();
+  InstDev I{};
+  I.k = d->k; I.half = d->half; I.H = d->H; I.E = d->E;
+  I.C = d->cfg.n_criteria; I.method = d->cfg.method; I.rule = d->cfg.pair_rule;
+  I.host_cpu = d->cfg.host_cpu; I.host_mem = d->cfg.host_mem; I.link_mbps = d->cfg.link_mbps;
+  for (int v = 0; v < kMaxC; ++v) I.W[v] = v < I.C ? d->cfg.weights[v] : 0.0;
+  I.L1 = d->d_L1;
+  I.cpu = d->d_state;
+  I.mem = d->d_state + d->H;
+  I.ctr = d->d_state + 2 * d->H;
+  I.pre = d->d_state + 3 * d->H;
+  I.res = d->d_state + 4 * d->H;
+  I.reqs = reinterpret_cast<const ReqRec*>(base + L.req);
+  I.c_lay = reinterpret_cast<const int4*>(base + L.c_lay);
+  I.e_lay = reinterpret_cast<const int4*>(base + L.e_lay);
+  I.p_coff = reinterpret_cast<const int32_t*>(base + L.pc);
+  I.p_eoff = reinterpret_cast<const int32_t*>(base + L.pe);
+  I.o_host = reinterpret_cast<int32_t*>(base + L.hof);
+  I.scr_links = kStaticMaxLinks;
+  I.scr_pods = 1;
+  I.scr_pe = reinterpret_cast<int4*>(base + L.pel);
+  I.scr_log = reinterpret_cast<PodLog*>(base + L.log);
+  I.err = d->d_err;
+  cudaStream_t st = d->stream;
+  const int32_t n = rec.n_c, m = rec.n_e, P = rec.n_p, H = d->H, C = d->cfg.n_criteria;
+  DC_CUDA(cudaMemcpyAsync(base + L.desc, &I, sizeof(I), cudaMemcpyHostToDevice, st));
+  DC_CUDA(cudaMemcpyAsync(base + L.req, &rec, sizeof(rec), cudaMemcpyHostToDevice, st));
+  if (n) DC_CUDA(cudaMemcpyAsync(base + L.c_lay, w->c_lay, n * sizeof(int4), cudaMemcpyHostToDevice, st));
+  if (m) DC_CUDA(cudaMemcpyAsync(base + L.e_lay, w->e_lay, m * sizeof(int4), cudaMemcpyHostToDevice, st));
+  DC_CUDA(cudaMemcpyAsync(base + L.pc, w->pc, (P + 1) * 4, cudaMemcpyHostToDevice, st));
+  DC_CUDA(cudaMemcpyAsync(base + L.pe, w->pe, (P + 1) * 4, cudaMemcpyHostToDevice, st));
+  if (n) DC_CUDA(cudaMemcpyAsync(base + L.hof, host_of, n * 4, cudaMemcpyHostToDevice, st));
+  DC_TRY(launch_rank(d->block, reinterpret_cast<const InstDev*>(base + L.desc), 0, pod,
+                     reinterpret_cast<const int32_t*>(base + L.hof),
+                     reinterpret_cast<int32_t*>(base + L.feas), reinterpret_cast<float*>(base + L.s32),
+                     reinterpret_cast<double*>(base + L.s64), reinterpret_cast<int32_t*>(base + L.crit),
+                     reinterpret_cast<int32_t*>(base + L.nv), d->smem, st));
+  int32_t nviable = 0;
+  if (feasible) DC_CUDA(cudaMemcpyAsync(feasible, base + L.feas, H * 4, cudaMemcpyDeviceToHost, st));
+  if (score32) DC_CUDA(cudaMemcpyAsync(score32, base + L.s32, H * 4, cudaMemcpyDeviceToHost, st));
+  if (score64) DC_CUDA(cudaMemcpyAsync(score64, base + L.s64, H * 8, cudaMemcpyDeviceToHost, st));
+  if (crit) DC_CUDA(cudaMemcpyAsync(crit, base + L.crit, (size_t)H * C * 4, cudaMemcpyDeviceToHost, st));
+  DC_CUDA(cudaMemcpyAsync(&nviable, base + L.nv, 4, cudaMemcpyDeviceToHost, st));
+  DC_CUDA(cudaStreamSynchronize(st));
+  return nviable;
+}

@@ -79,6 +79,8 @@ def lib():
         L.dc_query_state.argtypes = [C.c_void_p, C.c_int32, _i32p, C.c_int64]
         L.dc_rank_hosts.argtypes = [C.c_void_p, C.POINTER(_Request), C.c_int32, _i32p, _i32p,
                                     _f32p, _f64p, _i32p]
+        L.dc_rank_hosts_static.argtypes = [C.c_void_p, C.POINTER(_Request), C.c_int32, _i32p,
+                                           _i32p, _f32p, _f64p, _i32p]
         L.dc_reset.argtypes = [C.c_void_p]
         L.dc_plan_create.argtypes = [C.POINTER(C.c_void_p), C.c_int32, C.c_int32,
                                      C.POINTER(C.c_void_p)]
@@ -215,6 +217,20 @@ class DataCenter:
         nv = _check(lib().dc_rank_hosts(self.h, C.byref(r.s), pod, _p(ho, _i32p), _p(feas, _i32p),
                                         _p(s32, _f32p), _p(s64, _f64p), _p(crit, _i32p)),
                     "dc_rank_hosts")
+        return feas.astype(bool), s32, s64, crit.reshape(self.H, self.n_criteria), nv
+
+    def rank_hosts_static(self, q: Dict[str, np.ndarray], pod: int, host_of: np.ndarray):
+        """rank_hosts through the allocation-free entry point (device
+        temporaries in the library's static scratch array)."""
+        r = _Req(q)
+        ho = np.ascontiguousarray(host_of, np.int32)
+        feas = np.zeros(self.H, np.int32)
+        s32 = np.zeros(self.H, np.float32)
+        s64 = np.zeros(self.H, np.float64)
+        crit = np.zeros(self.H * self.n_criteria, np.int32)
+        nv = _check(lib().dc_rank_hosts_static(self.h, C.byref(r.s), pod, _p(ho, _i32p),
+                                               _p(feas, _i32p), _p(s32, _f32p), _p(s64, _f64p),
+                                               _p(crit, _i32p)), "dc_rank_hosts_static")
         return feas.astype(bool), s32, s64, crit.reshape(self.H, self.n_criteria), nv
 
     def reset(self) -> None:
