@@ -61,6 +61,7 @@ namespace dcs {
 struct Ctx {
   // instance
   int32_t k, half, H, E, C, method, link_mbps;
+  int32_t diff;           // AHP with the difference rule (exact fixed point)
   int32_t gs;             // lanes per pod group in the table pass (pow2 >= half)
   int32_t ea0, ac0, ld;   // link slots: edge-agg base, agg-core base, row stride
   unsigned long long mh;  // ceil(2^32 / half): x / half == (x * mh) >> 32
@@ -97,6 +98,8 @@ struct Ctx {
   int32_t commit_ok;
   int32_t arrive;
   int32_t ndec;
+  int32_t nvc;      // viable hosts counted by the AHP DIFF compaction
+  double wscore;    // AHP DIFF: exact global priority of the winner
 };
 
 struct Sm {
@@ -667,6 +670,116 @@ static __device__ void column_fp64(const Sm& s) {
   __syncthreads();
 }
 
+// ------------------------------------------------------------- AHP DIFF
+//
+// Local priorities under the difference rule (Sec. V-B), exactly as the
+// oracle defines them: for criterion v over the F viable hosts,
+//   A(d) = d * 2^64 (d > 0), 2^64 (d = 0 or -1), round(2^64 / -d) (d < -1),
+//   S_j = sum_i A(x_i - x_j),  I_j = rint(2^64 / double(S_j * 2^-64)),
+//   term(d, I) = q * I for an integer entry q (d >= -1, q = max(d, 1)),
+//                floor((round(2^64 / -d) * I + 2^63) / 2^64) otherwise,
+//   L2_i = (double(sum_j term(x_i - x_j, I_j)) * 2^-64) / F,
+// sums exact in unsigned 128-bit integers (order-free), every floating-point
+// step one IEEE binary64 operation rounded to nearest.  F = 1 gives L2 = 1.
+// The global priority PG = sum_v L1_v * L2_v is then an exact FP64 value, so
+// the selection needs no guard band.  Cost O(F^2) per criterion.
+
+static __device__ __forceinline__ unsigned long long recip_long(unsigned long long m) {
+  // floor((2^65 + m) / (2m)) by long division over 32-bit limbs, m < 2^31
+  const unsigned long long d = 2ull * m;
+  unsigned long long r = 2ull % d;
+  unsigned long long cur = r << 32;
+  const unsigned long long q1 = cur / d;
+  r = cur % d;
+  cur = (r << 32) | m;
+  return (q1 << 32) | (cur / d);
+}
+static __device__ __forceinline__ unsigned long long recip_q64(const unsigned long long* tab, int m) {
+  return m < kRecipTable ? tab[m] : recip_long((unsigned long long)m);
+}
+// 128-bit unsigned integer to double, correctly rounded to nearest-even
+static __device__ double u128_to_double(unsigned long long lo, unsigned long long hi) {
+  if (hi == 0) return __ull2double_rn(lo);
+  const int sbits = 64 - __clzll((long long)hi);  // significant bits of hi, 1..64
+  unsigned long long top, rest;
+  if (sbits == 64) {
+    top = hi;
+    rest = lo;
+  } else {
+    top = (hi << (64 - sbits)) | (lo >> sbits);
+    rest = lo << (64 - sbits);
+  }
+  top |= rest != 0 ? 1ull : 0ull;  // sticky bit
+  return __dmul_rn(__ull2double_rn(top), ldexp(1.0, sbits));
+}
+static __device__ __forceinline__ void add128(unsigned long long& lo, unsigned long long& hi,
+                                              unsigned long long alo, unsigned long long ahi) {
+  lo += alo;
+  hi += ahi + (lo < alo ? 1ull : 0ull);
+}
+
+// Compacts the viable hosts with their criteria, then computes the global
+// priority of each into I.dx_pg (block-wide; ends with a barrier).
+template <int B>
+static __device__ void diff_scores(const Sm& s, const InstDev& I) {
+  Ctx& c = *s.c;
+  const int tid = threadIdx.x, H = c.H, C = c.C;
+  if (tid == 0) c.nvc = 0;
+  __syncthreads();
+  for (int u = tid; u < H; u += B) {
+    int32_t x[kMaxC];
+    if (host_crit<B>(s, u, x)) {
+      const int p = atomicAdd(&c.nvc, 1);
+      I.dx_idx[p] = u;
+      for (int v = 0; v < C; ++v) I.dx_val[v * H + p] = x[v];
+    }
+  }
+  __syncthreads();
+  const int F = c.nvc;
+  for (int v = 0; v < C; ++v) {
+    const int32_t* X = I.dx_val + v * H;
+    if (F > 1) {
+      for (int p = tid; p < F; p += B) {
+        const int xp = X[p];
+        unsigned long long lo = 0, hi = 0;
+        for (int q = 0; q < F; ++q) {
+          const int d = X[q] - xp;
+          if (d > 0) add128(lo, hi, 0ull, (unsigned long long)d);
+          else if (d >= -1) add128(lo, hi, 0ull, 1ull);
+          else add128(lo, hi, recip_q64(I.recip, -d), 0ull);
+        }
+        const double sj = __dmul_rn(u128_to_double(lo, hi), 0x1p-64);
+        const double inv = __ddiv_rn(1.0, sj);
+        I.dx_inv[p] = __double2ull_rn(__dmul_rn(inv, 0x1p64));
+      }
+      __syncthreads();
+    }
+    for (int p = tid; p < F; p += B) {
+      double l2 = 1.0;
+      if (F > 1) {
+        const int xp = X[p];
+        unsigned long long lo = 0, hi = 0;
+        for (int q = 0; q < F; ++q) {
+          const int d = xp - X[q];
+          const unsigned long long Iq = I.dx_inv[q];
+          if (d >= -1) {
+            const unsigned long long qq = d > 0 ? (unsigned long long)d : 1ull;
+            add128(lo, hi, qq * Iq, __umul64hi(qq, Iq));
+          } else {
+            const unsigned long long R = recip_q64(I.recip, -d);
+            const unsigned long long plo = R * Iq, phi = __umul64hi(R, Iq);
+            add128(lo, hi, phi + (plo >> 63), 0ull);
+          }
+        }
+        l2 = __ddiv_rn(__dmul_rn(u128_to_double(lo, hi), 0x1p-64), (double)F);
+      }
+      const double pg = v == 0 ? 0.0 : I.dx_pg[p];
+      I.dx_pg[p] = __dadd_rn(pg, __dmul_rn(c.L1[v], l2));
+    }
+    __syncthreads();
+  }
+}
+
 // block-wide (max, lowest index, number of hosts at the max, second
 // distinct max) over FP32 selection scores
 struct Sel { float m1; int idx; int cnt; float m2; };
@@ -790,6 +903,40 @@ static __device__ void pick_host(const Sm& s) {
   __syncthreads();
 }
 
+// a6 under AHP DIFF: exact FP64 argmax (lowest index on ties) over the viable
+// hosts whose commit can succeed and that did not fail one.
+template <int B>
+static __device__ void pick_diff(const Sm& s, const InstDev& I) {
+  Ctx& c = *s.c;
+  const int tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
+  constexpr int NW = B / 32;
+  Sel64 b = {-1.0, INT_MAX};
+  for (int p = tid; p < c.nvc; p += B) {
+    const int u = I.dx_idx[p];
+    if (!((s.trymask[u % B] >> (u / B)) & 1u) && commit_possible<B>(s, u))
+      b = sel64_combine(b, Sel64{I.dx_pg[p], u});
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    Sel64 q = {__shfl_xor_sync(0xffffffffu, b.s, o), __shfl_xor_sync(0xffffffffu, b.idx, o)};
+    b = sel64_combine(b, q);
+  }
+  Sel64* ws64 = reinterpret_cast<Sel64*>(s.sel);
+  if (lane == 0) ws64[w] = b;
+  __syncthreads();
+  if (w == 0) {
+    Sel64 t = lane < NW ? ws64[lane] : Sel64{-1.0, INT_MAX};
+    for (int o = 16; o > 0; o >>= 1) {
+      Sel64 q = {__shfl_xor_sync(0xffffffffu, t.s, o), __shfl_xor_sync(0xffffffffu, t.idx, o)};
+      t = sel64_combine(t, q);
+    }
+    if (lane == 0) {
+      c.winner = t.s < 0.0 ? -1 : t.idx;
+      c.wscore = t.s;
+    }
+  }
+  __syncthreads();
+}
+
 // Widest shortest path between hosts hs != ht (warp-wide; every lane gets
 // the result).  Ties: lowest aggregation index a, then lowest core index c.
 // links[] receive global link ids.
@@ -857,6 +1004,7 @@ static __device__ void commit_warp(const Sm& s, const InstDev& I, int g, Pre& nx
       L->S2[v] = c.S2[v];
     }
     L->n = c.n;
+    L->score = c.wscore;
   }
   __syncwarp();
   int done = 0;  // peer links committed so far
@@ -991,6 +1139,7 @@ static __device__ void load_instance(const Sm& s, const InstDev& I) {
   if (tid == 0) {
     c.k = I.k; c.half = I.half; c.H = I.H; c.E = I.E; c.C = I.C; c.method = I.method;
     c.link_mbps = I.link_mbps;
+    c.diff = (I.method == DC_AHP && I.rule == DC_PAIR_DIFF) ? 1 : 0;
     int gs = 1;
     while (gs < I.half) gs <<= 1;
     c.gs = gs;
@@ -1075,9 +1224,13 @@ static __device__ bool decide_pod(const Sm& s, const InstDev& I, int g, Pre& nxt
   const int tid = threadIdx.x;
   if (c.npe > 0) build_tables<B>(s);  // ends with a barrier
   column_stats<B>(s);
+  if (c.diff) diff_scores<B>(s, I);
   bool placed = false;
   for (;;) {
-    pick_host<B>(s);
+    if (c.diff)
+      pick_diff<B>(s, I);
+    else
+      pick_host<B>(s);
     if (c.winner < 0) break;
     if (tid < 32) commit_warp<B>(s, I, g, nxt);
     __syncthreads();
@@ -1101,6 +1254,10 @@ static __device__ void pod_scores(const Sm& s, const InstDev& I, int n_placed) {
   const Ctx& c = *s.c;
   for (int g = threadIdx.x; g < n_placed; g += B) {
     const PodLog* L = I.scr_log + g;
+    if (c.diff) {
+      I.o_score[c.p_off + g] = L->score;
+      continue;
+    }
     double norm[kMaxC], Ap[kMaxC], An[kMaxC], Td[kMaxC];
     int32_t x[kMaxC];
     for (int v = 0; v < c.C; ++v) {
@@ -1215,10 +1372,18 @@ __global__ void __launch_bounds__(B, 1) k_rank(const InstDev* __restrict__ inst,
     int32_t x[kMaxC];
     const bool f = host_crit<B>(s, u, x);
     feas[u] = f ? 1 : 0;
-    s32[u] = f ? closeness32(c, x) : __int_as_float(0x7fc00000);
-    s64[u] = f ? score64(c.method, c.C, c.W, c.L1, c.norm, c.Ap, c.An, c.Td, x)
-               : __longlong_as_double(0x7ff8000000000000ll);
+    s32[u] = f && !c.diff ? closeness32(c, x) : __int_as_float(0x7fc00000);
+    s64[u] = f && !c.diff ? score64(c.method, c.C, c.W, c.L1, c.norm, c.Ap, c.An, c.Td, x)
+                          : __longlong_as_double(0x7ff8000000000000ll);
     for (int v = 0; v < c.C; ++v) crit[(int64_t)u * c.C + v] = x[v];
+  }
+  if (c.diff) {
+    diff_scores<B>(s, I);
+    for (int p = threadIdx.x; p < c.nvc; p += B) {
+      const int u = I.dx_idx[p];
+      s64[u] = I.dx_pg[p];
+      s32[u] = (float)I.dx_pg[p];
+    }
   }
   if (threadIdx.x == 0) *nviable = c.n;
 }

@@ -60,7 +60,11 @@ struct PodLog {
   int32_t mx[kMaxC], mn[kMaxC];
   int32_t pad;
   long long S1[kMaxC], S2[kMaxC];
+  double score;  // AHP DIFF: the exact global priority of the chosen host
 };
+
+// Reciprocals round(2^64 / m) for 2 <= m < kRecipTable (AHP DIFF).
+constexpr int32_t kRecipTable = 1 << 16;
 
 // Everything one instance's thread block needs, in global memory.
 struct InstDev {
@@ -87,6 +91,14 @@ struct InstDev {
   int32_t scr_pods;   // capacity of scr_log, in pods
   int4* scr_pe;       // peer links of the pod being placed
   PodLog* scr_log;    // [pods of the current request]
+  // AHP DIFF scratch, [H] each (null for the other methods): viable host
+  // list, criteria of the viable hosts [C][H], inverse column sums (Q64),
+  // global priorities; and the shared reciprocal table
+  int32_t* dx_idx;
+  int32_t* dx_val;
+  unsigned long long* dx_inv;
+  double* dx_pg;
+  const unsigned long long* recip;
   int32_t* err;       // [1] 0 or a DC_E_* code
   // [3] pod decisions, host rankings (accumulated), launch start clock (min)
   unsigned long long* counters;
@@ -147,5 +159,6 @@ int launch_rank(int block, const InstDev* d_inst, int32_t req, int32_t pod, cons
                 int32_t* feas, float* s32, double* s64, int32_t* crit, int32_t* nviable,
                 size_t smem, void* stream);
 int launch_weights(int C, int rule, const double* d_W, double* d_L1, void* stream);
+int launch_recip_table(unsigned long long* d_tab, void* stream);
 
 }  // namespace dcs

@@ -33,6 +33,26 @@ __global__ void k_weights(int C, int rule, const double* __restrict__ W, double*
   }
 }
 
+// round(2^64 / m) = floor((2^65 + m) / (2m)) for 2 <= m < kRecipTable, by
+// long division over 32-bit limbs (the quotient is below 2^64).
+__global__ void k_recip(unsigned long long* __restrict__ tab) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= kRecipTable) return;
+  if (m < 2) {
+    tab[m] = 0;
+    return;
+  }
+  const unsigned long long d = 2ull * (unsigned long long)m;
+  // numerator limbs (base 2^32): [2, 0, m]
+  unsigned long long r = 2ull % d;
+  unsigned long long cur = (r << 32) | 0ull;
+  const unsigned long long q1 = cur / d;
+  r = cur % d;
+  cur = (r << 32) | (unsigned long long)m;
+  const unsigned long long q0 = cur / d;
+  tab[m] = (q1 << 32) | q0;
+}
+
 #define DC_DECL(B)                                                                          \
   cudaError_t set_smem_attr_##B(size_t smem);                                               \
   cudaError_t launch_schedule_##B(const InstDev* d_insts, int n, size_t smem, cudaStream_t st); \
@@ -92,6 +112,11 @@ int launch_rank(int block, const InstDev* d_inst, int32_t req, int32_t pod, cons
     default: return DC_E_INVAL;
   }
   return e == cudaSuccess ? DC_OK : DC_E_CUDA;
+}
+
+int launch_recip_table(unsigned long long* d_tab, void* stream) {
+  k_recip<<<kRecipTable / 256, 256, 0, (cudaStream_t)stream>>>(d_tab);
+  return cudaGetLastError() == cudaSuccess ? DC_OK : DC_E_CUDA;
 }
 
 int launch_weights(int C, int rule, const double* d_W, double* d_L1, void* stream) {

@@ -105,6 +105,24 @@ int pick_block(int k) {
 
 size_t g_smem_max = 0;
 bool g_configured = false;
+// round(2^64 / m) table of AHP DIFF, one per device, built on first use
+unsigned long long* g_recip_dev[64] = {nullptr};
+
+int recip_table(cudaStream_t st, const unsigned long long** out) {
+  int dev = 0;
+  DC_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return DC_E_INVAL;
+  if (!g_recip_dev[dev]) {
+    unsigned long long* t = nullptr;
+    if (cudaMalloc((void**)&t, sizeof(unsigned long long) * kRecipTable) != cudaSuccess)
+      return DC_E_NOMEM;
+    DC_TRY(launch_recip_table(t, st));
+    DC_CUDA(cudaStreamSynchronize(st));
+    g_recip_dev[dev] = t;
+  }
+  *out = g_recip_dev[dev];
+  return DC_OK;
+}
 
 int ensure_configured() {
   if (g_configured) return DC_OK;
@@ -132,6 +150,10 @@ struct dc_t {
   double* d_W = nullptr;
   double* d_L1 = nullptr;
   int32_t* d_err = nullptr;
+  // AHP DIFF scratch (one allocation): host list [H], criteria [C][H],
+  // inverse column sums [H] (u64), global priorities [H] (f64)
+  unsigned char* d_dx = nullptr;
+  const unsigned long long* d_recip = nullptr;
   // host request store (pinned): per-container and per-link records in pod
   // order and the per-pod ranges (see ReqRec)
   PinnedVec<int4> c_lay, e_lay;
@@ -205,7 +227,6 @@ int validate_config(const dc_config* c) {
   if (c->n_criteria != 4 && c->n_criteria != 6) return DC_E_INVAL;
   if (c->method != DC_TOPSIS && c->method != DC_AHP) return DC_E_INVAL;
   if (c->pair_rule != DC_PAIR_RATIO && c->pair_rule != DC_PAIR_DIFF) return DC_E_INVAL;
-  if (c->method == DC_AHP && c->pair_rule == DC_PAIR_DIFF) return DC_E_INVAL;  // not built yet
   double s = 0.0;
   for (int v = 0; v < c->n_criteria; ++v) {
     if (!(c->weights[v] >= 0.0) || !std::isfinite(c->weights[v])) return DC_E_INVAL;
@@ -393,6 +414,14 @@ InstDev make_desc(dc_t* d, const int32_t* d_ops, int n_ops, unsigned long long* 
   I.scr_pods = d->scr_pods;
   I.scr_pe = d->d_scr_pe.p;
   I.scr_log = d->d_scr_log.p;
+  if (d->d_dx) {
+    const size_t H = (size_t)d->H;
+    I.dx_idx = reinterpret_cast<int32_t*>(d->d_dx);
+    I.dx_val = reinterpret_cast<int32_t*>(d->d_dx + 4 * H);
+    I.dx_inv = reinterpret_cast<unsigned long long*>(d->d_dx + 4 * H * (1 + kMaxC));
+    I.dx_pg = reinterpret_cast<double*>(d->d_dx + 4 * H * (1 + kMaxC) + 8 * H);
+  }
+  I.recip = d->d_recip;
   I.err = d->d_err;
   I.counters = counters;
   return I;
@@ -548,6 +577,12 @@ int dc_create(const dc_config* cfg, void* cuda_stream, dc_t** out) {
         cudaMemset(d->d_err, 0, sizeof(int32_t)) != cudaSuccess)
       rc = DC_E_CUDA;
   }
+  if (rc == DC_OK && cfg->method == DC_AHP && cfg->pair_rule == DC_PAIR_DIFF) {
+    // 4 + 4C + 8 + 8 bytes per host (4-byte sections first keep 8-byte alignment)
+    if (cudaMalloc((void**)&d->d_dx, (size_t)H * (4 + 4 * kMaxC + 16)) != cudaSuccess)
+      rc = DC_E_NOMEM;
+    if (rc == DC_OK) rc = recip_table(d->stream, &d->d_recip);
+  }
   if (rc == DC_OK) rc = launch_weights(cfg->n_criteria, cfg->pair_rule, d->d_W, d->d_L1, d->stream);
   if (rc == DC_OK) rc = cuda_rc(cudaStreamSynchronize(d->stream));
   if (rc != DC_OK) {
@@ -581,6 +616,7 @@ void dc_destroy(dc_t* d) {
   if (d->d_W) cudaFree(d->d_W);
   if (d->d_L1) cudaFree(d->d_L1);
   if (d->d_err) cudaFree(d->d_err);
+  if (d->d_dx) cudaFree(d->d_dx);
   delete d;
 }
 
@@ -941,6 +977,8 @@ int dc_rank_hosts(dc_t* d, const dc_request* q, int32_t pod, const int32_t* host
     tmp.d_state = d->d_state;
     tmp.d_L1 = d->d_L1;
     tmp.d_err = d->d_err;
+    tmp.d_dx = d->d_dx;
+    tmp.d_recip = d->d_recip;
     InstDev I = make_desc(&tmp, nullptr, 0, nullptr);
     if (r.n_c) rc = cuda_rc(cudaMemcpyAsync(d_host_of, host_of, r.n_c * 4, cudaMemcpyHostToDevice, st));
     if (rc == DC_OK) rc = cuda_rc(cudaMemcpyAsync(d_desc, &I, sizeof(I), cudaMemcpyHostToDevice, st));
@@ -971,7 +1009,7 @@ int dc_rank_hosts(dc_t* d, const dc_request* q, int32_t pod, const int32_t* host
   tmp.m_path.release(); tmp.m_status.release(); tmp.m_ndec.release(); tmp.m_score.release();
   tmp.m_tdone.release();
   cudaStreamSynchronize(st);
-  tmp.d_state = nullptr; tmp.d_L1 = nullptr; tmp.d_err = nullptr;
+  tmp.d_state = nullptr; tmp.d_L1 = nullptr; tmp.d_err = nullptr; tmp.d_dx = nullptr;
   return rc == DC_OK ? nviable : rc;
 }
 
@@ -1154,6 +1192,14 @@ extern "C" int dc_rank_hosts_static(dc_t* d, const dc_request* q, int32_t pod,
   I.scr_pe = reinterpret_cast<int4*>(base + L.pel);
   I.scr_log = reinterpret_cast<PodLog*>(base + L.log);
   I.err = d->d_err;
+  if (d->d_dx) {  // the instance's own AHP DIFF scratch (allocated by dc_create)
+    const size_t Hh = (size_t)d->H;
+    I.dx_idx = reinterpret_cast<int32_t*>(d->d_dx);
+    I.dx_val = reinterpret_cast<int32_t*>(d->d_dx + 4 * Hh);
+    I.dx_inv = reinterpret_cast<unsigned long long*>(d->d_dx + 4 * Hh * (1 + kMaxC));
+    I.dx_pg = reinterpret_cast<double*>(d->d_dx + 4 * Hh * (1 + kMaxC) + 8 * Hh);
+  }
+  I.recip = d->d_recip;
   cudaStream_t st = d->stream;
   const int32_t n = rec.n_c, m = rec.n_e, P = rec.n_p, H = d->H, C = d->cfg.n_criteria;
   DC_CUDA(cudaMemcpyAsync(base + L.desc, &I, sizeof(I), cudaMemcpyHostToDevice, st));

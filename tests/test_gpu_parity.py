@@ -30,13 +30,16 @@ def stream():
     return torch.cuda.Stream()
 
 
-@pytest.mark.parametrize("method", [W.TOPSIS, W.AHP])
+METHODS = [(W.TOPSIS, W.RATIO), (W.AHP, W.RATIO), (W.AHP, W.DIFF)]
+
+
+@pytest.mark.parametrize("method,rule", METHODS)
 @pytest.mark.parametrize("scheme", ["flat", "clustering", "network"])
-def test_small_config(ds, stream, method, scheme):
-    inst = W.small(method=method, scheme=scheme).instances[0]
+def test_small_config(ds, stream, method, rule, scheme):
+    inst = W.small(method=method, pair_rule=rule, scheme=scheme).instances[0]
     dc = ds.load_instance(inst, stream=stream)
     ds.schedule([dc])
-    check_instance(dc, inst, where="small/%d/%s" % (method, scheme))
+    check_instance(dc, inst, where="small/%d/%d/%s" % (method, rule, scheme))
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
@@ -45,21 +48,23 @@ def test_small_intervals_and_pods(ds, stream, seed):
     reqs = [W.gen_request(rng, int(rng.integers(2, 12)), p_edge=0.5,
                           bw=lambda r, m: r.integers(10, 400, m), max_pod=3, intervals=True,
                           intra_pod_links=True) for _ in range(40)]
-    for method in (W.TOPSIS, W.AHP):
-        inst = W.Instance(4, 16, 32, 1000, 6, method, W.RATIO, W.WEIGHTS[6]["network"],
+    for method, rule in METHODS:
+        inst = W.Instance(4, 16, 32, 1000, 6, method, rule, W.WEIGHTS[6]["network"],
                           None, None, None, W.pack_requests(reqs))
         dc = ds.load_instance(inst, stream=stream)
         ds.schedule([dc])
-        check_instance(dc, inst, where="pods/%d/%d" % (seed, method))
+        check_instance(dc, inst, where="pods/%d/%d/%d" % (seed, method, rule))
 
 
 @pytest.mark.parametrize("k,n_req", [(8, 120), (16, 60)])
-@pytest.mark.parametrize("method", [W.TOPSIS, W.AHP])
-def test_k16_prefix(ds, stream, k, n_req, method):
-    inst = W.k16(k=k, n_requests=n_req, method=method).instances[0]
+@pytest.mark.parametrize("method,rule", METHODS)
+def test_k16_prefix(ds, stream, k, n_req, method, rule):
+    if rule == W.DIFF:
+        n_req = n_req // 4  # O(F^2) per criterion and decision in both implementations
+    inst = W.k16(k=k, n_requests=n_req, method=method, pair_rule=rule).instances[0]
     dc = ds.load_instance(inst, stream=stream)
     ds.schedule([dc])
-    check_instance(dc, inst, where="k%d/%d" % (k, method))
+    check_instance(dc, inst, where="k%d/%d/%d" % (k, method, rule))
 
 
 def test_k32_single_block(ds, stream):
@@ -134,12 +139,12 @@ def test_plan_graph_replay(ds, stream):
         check_instance(dc, inst, where="plan")
 
 
-@pytest.mark.parametrize("method", [W.TOPSIS, W.AHP])
-def test_rank_hosts_scores(ds, stream, method):
+@pytest.mark.parametrize("method,rule", METHODS)
+def test_rank_hosts_scores(ds, stream, method, rule):
     """Per-host viability and criteria exact, FP64 scores bit-exact, FP32
     scores within 1e-6 relative of the oracle, for pods with placed
     neighbours on a pre-loaded k=16 fat-tree."""
-    inst = W.k16(n_requests=20, method=method).instances[0]
+    inst = W.k16(n_requests=20, method=method, pair_rule=rule).instances[0]
     dc = ds.DataCenter.from_instance(inst, stream=stream)
     odc = O.OracleDC.from_instance(inst)
     rng = np.random.default_rng(7)
