@@ -121,13 +121,21 @@ struct Sm {
   int4* curc;  // [32] container records of the pod being placed
 };
 
-static __device__ __forceinline__ Sm carve(unsigned char* base, int k, int B) {
-  SmemLayout L = smem_layout(k, B, sizeof(Ctx));
+static __device__ __forceinline__ Sm carve(unsigned char* base, const InstDev& I, int B) {
+  const int k = I.k;
+  SmemLayout L = smem_layout(k, B, sizeof(Ctx), !I.state_global);
   Sm s;
   s.c = reinterpret_cast<Ctx*>(base + L.ctx);
-  s.cm = reinterpret_cast<uint32_t*>(base + L.cm);
-  s.ctr = reinterpret_cast<int32_t*>(base + L.ctr);
-  s.lk = reinterpret_cast<int32_t*>(base + L.lk);
+  if (I.state_global) {
+    // packed state in global scratch: cm[H], ctr[H], link slots
+    s.cm = reinterpret_cast<uint32_t*>(I.gstate);
+    s.ctr = I.gstate + I.H;
+    s.lk = I.gstate + 2 * I.H;
+  } else {
+    s.cm = reinterpret_cast<uint32_t*>(base + L.cm);
+    s.ctr = reinterpret_cast<int32_t*>(base + L.ctr);
+    s.lk = reinterpret_cast<int32_t*>(base + L.lk);
+  }
   const int E = k * k / 2;
   int32_t* t = reinterpret_cast<int32_t*>(base + L.tab);
   s.T1 = t; s.T1h = t + E; s.T2 = t + 2 * E; s.S1 = t + 3 * E; s.S1h = t + 4 * E;
@@ -1321,7 +1329,7 @@ template <int B, int HPT>
 __global__ void __launch_bounds__(B, 1) k_schedule(const InstDev* __restrict__ insts) {
   extern __shared__ __align__(16) unsigned char smem[];
   const InstDev& I = insts[blockIdx.x];
-  const Sm s = carve(smem, I.k, B);
+  const Sm s = carve(smem, I, B);
   if (threadIdx.x == 0) atomicMin(&I.counters[2], globaltimer_ns());
   load_instance<B>(s, I);
   for (int op = 0; op < I.n_ops; ++op) {
@@ -1351,7 +1359,7 @@ __global__ void __launch_bounds__(B, 1) k_rank(const InstDev* __restrict__ inst,
                                               int32_t* crit, int32_t* nviable) {
   extern __shared__ __align__(16) unsigned char smem[];
   const InstDev& I = *inst;
-  const Sm s = carve(smem, I.k, B);
+  const Sm s = carve(smem, I, B);
   load_instance<B>(s, I);
   load_request<B>(s, I, r, host_of);
   if (s.c->hof != s.st_hof) {

@@ -26,7 +26,9 @@ constexpr int32_t kOpRelease = 1 << 30;
 // peer-link word in scratch: link index, | kPeSrc when the pod holds the src end
 constexpr int32_t kPeSrc = 1 << 30;
 constexpr int32_t kMaxLinksPerRequest = 1 << 18;
-constexpr int32_t kMaxK = 32;
+constexpr int32_t kMaxK = 48;
+// largest k whose data-center state fits one block's shared memory
+constexpr int32_t kMaxKSmem = 32;
 constexpr int kHash = 256;   // slots of the per-pod peer-host hash table
 constexpr int kPeS = 256;    // peer links of one pod kept in shared memory
 constexpr int kMaxBlock = 1024;
@@ -89,6 +91,10 @@ struct InstDev {
   int32_t n_ops;
   int32_t scr_links;  // capacity of scr_pe, in links
   int32_t scr_pods;   // capacity of scr_log, in pods
+  // state_global: the packed state (cm[H], ctr[H], link slots) lives in
+  // gstate (global scratch, L2-resident) instead of shared memory
+  int32_t state_global;
+  int32_t* gstate;
   int4* scr_pe;       // peer links of the pod being placed
   PodLog* scr_log;    // [pods of the current request]
   // AHP DIFF scratch, [H] each (null for the other methods): viable host
@@ -121,15 +127,16 @@ DC_HD inline size_t link_slots(int k) {
   return H + 2 * half * (E + 1);
 }
 
-DC_HD inline SmemLayout smem_layout(int k, int block, size_t ctx_bytes) {
+DC_HD inline SmemLayout smem_layout(int k, int block, size_t ctx_bytes, bool state_smem = true) {
   SmemLayout L;
-  const size_t H = (size_t)k * k * k / 4, E = (size_t)k * k / 2;
+  const size_t E = (size_t)k * k / 2;
+  const size_t H = state_smem ? (size_t)k * k * k / 4 : 0;
   const size_t nw = (size_t)block / 32;
   size_t o = 0;
   L.ctx = o; o = align_up(o + ctx_bytes, 16);
   L.cm = o; o = align_up(o + 4 * H, 16);
   L.ctr = o; o = align_up(o + 4 * H, 16);
-  L.lk = o; o = align_up(o + 4 * link_slots(k), 16);
+  L.lk = o; o = align_up(o + (state_smem ? 4 * link_slots(k) : 0), 16);
   L.tab = o; o = align_up(o + 7 * 4 * E, 16);
   L.cp = o; o = align_up(o + 4 * (size_t)k, 16);
   L.tmark = o; o = align_up(o + 4 * (size_t)block, 16);

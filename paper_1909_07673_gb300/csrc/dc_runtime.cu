@@ -154,6 +154,10 @@ struct dc_t {
   // inverse column sums [H] (u64), global priorities [H] (f64)
   unsigned char* d_dx = nullptr;
   const unsigned long long* d_recip = nullptr;
+  // fat-trees too large for one block's shared memory keep the packed state
+  // (cm[H], ctr[H], link slots) in this global scratch
+  bool state_global = false;
+  int32_t* d_gstate = nullptr;
   // host request store (pinned): per-container and per-link records in pod
   // order and the per-pod ranges (see ReqRec)
   PinnedVec<int4> c_lay, e_lay;
@@ -422,6 +426,8 @@ InstDev make_desc(dc_t* d, const int32_t* d_ops, int n_ops, unsigned long long* 
     I.dx_pg = reinterpret_cast<double*>(d->d_dx + 4 * H * (1 + kMaxC) + 8 * H);
   }
   I.recip = d->d_recip;
+  I.state_global = d->state_global ? 1 : 0;
+  I.gstate = d->d_gstate;
   I.err = d->d_err;
   I.counters = counters;
   return I;
@@ -536,7 +542,13 @@ int dc_create(const dc_config* cfg, void* cuda_stream, dc_t** out) {
   d->stream = (cudaStream_t)cuda_stream;
   d->block = pick_block(d->k);
   d->smem = smem_layout(d->k, d->block, ctx_bytes()).total;
-  if (d->smem > g_smem_max || d->H > d->block * max_hosts_per_thread(d->block)) {
+  if (d->k > kMaxKSmem || d->smem > g_smem_max) {
+    d->state_global = true;
+    d->block = 1024;
+    d->smem = smem_layout(d->k, d->block, ctx_bytes(), false).total;
+  }
+  // hosts per thread are tracked in one 32-bit mask word per thread
+  if (d->smem > g_smem_max || d->H > 32 * d->block) {
     delete d;
     return DC_E_INVAL;
   }
@@ -577,6 +589,10 @@ int dc_create(const dc_config* cfg, void* cuda_stream, dc_t** out) {
         cudaMemset(d->d_err, 0, sizeof(int32_t)) != cudaSuccess)
       rc = DC_E_CUDA;
   }
+  if (rc == DC_OK && d->state_global &&
+      cudaMalloc((void**)&d->d_gstate, sizeof(int32_t) * (2 * (size_t)H + link_slots(d->k))) !=
+          cudaSuccess)
+    rc = DC_E_NOMEM;
   if (rc == DC_OK && cfg->method == DC_AHP && cfg->pair_rule == DC_PAIR_DIFF) {
     // 4 + 4C + 8 + 8 bytes per host (4-byte sections first keep 8-byte alignment)
     if (cudaMalloc((void**)&d->d_dx, (size_t)H * (4 + 4 * kMaxC + 16)) != cudaSuccess)
@@ -617,6 +633,7 @@ void dc_destroy(dc_t* d) {
   if (d->d_L1) cudaFree(d->d_L1);
   if (d->d_err) cudaFree(d->d_err);
   if (d->d_dx) cudaFree(d->d_dx);
+  if (d->d_gstate) cudaFree(d->d_gstate);
   delete d;
 }
 
@@ -979,6 +996,10 @@ int dc_rank_hosts(dc_t* d, const dc_request* q, int32_t pod, const int32_t* host
     tmp.d_err = d->d_err;
     tmp.d_dx = d->d_dx;
     tmp.d_recip = d->d_recip;
+    tmp.state_global = d->state_global;
+    tmp.d_gstate = d->d_gstate;
+    tmp.block = d->block;
+    tmp.smem = d->smem;
     InstDev I = make_desc(&tmp, nullptr, 0, nullptr);
     if (r.n_c) rc = cuda_rc(cudaMemcpyAsync(d_host_of, host_of, r.n_c * 4, cudaMemcpyHostToDevice, st));
     if (rc == DC_OK) rc = cuda_rc(cudaMemcpyAsync(d_desc, &I, sizeof(I), cudaMemcpyHostToDevice, st));
@@ -1010,6 +1031,7 @@ int dc_rank_hosts(dc_t* d, const dc_request* q, int32_t pod, const int32_t* host
   tmp.m_tdone.release();
   cudaStreamSynchronize(st);
   tmp.d_state = nullptr; tmp.d_L1 = nullptr; tmp.d_err = nullptr; tmp.d_dx = nullptr;
+  tmp.d_gstate = nullptr;
   return rc == DC_OK ? nviable : rc;
 }
 
@@ -1200,6 +1222,8 @@ extern "C" int dc_rank_hosts_static(dc_t* d, const dc_request* q, int32_t pod,
     I.dx_pg = reinterpret_cast<double*>(d->d_dx + 4 * Hh * (1 + kMaxC) + 8 * Hh);
   }
   I.recip = d->d_recip;
+  I.state_global = d->state_global ? 1 : 0;
+  I.gstate = d->d_gstate;
   cudaStream_t st = d->stream;
   const int32_t n = rec.n_c, m = rec.n_e, P = rec.n_p, H = d->H, C = d->cfg.n_criteria;
   DC_CUDA(cudaMemcpyAsync(base + L.desc, &I, sizeof(I), cudaMemcpyHostToDevice, st));

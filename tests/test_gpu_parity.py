@@ -76,6 +76,17 @@ def test_k32_single_block(ds, stream):
     check_instance(dc, inst, where="k32")
 
 
+@pytest.mark.parametrize("method,rule", [(W.TOPSIS, W.RATIO), (W.AHP, W.RATIO)])
+def test_k48_global_state(ds, stream, method, rule):
+    """k = 48 (27,648 hosts, the paper-scale fat-tree): the state lives in an
+    L2-resident global copy instead of shared memory.  Pods of 1-8
+    containers, intra-pod links, Pareto bandwidths, 0-100 % pre-load."""
+    inst = W.k48(n_requests=3, method=method, pair_rule=rule).instances[0]
+    dc = ds.load_instance(inst, stream=stream)
+    ds.schedule([dc])
+    check_instance(dc, inst, where="k48/%d" % method)
+
+
 def test_incremental_schedules_and_releases(ds, stream):
     """Submit / schedule / release in several launches; FCFS state carried
     across launches."""
