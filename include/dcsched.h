@@ -216,6 +216,43 @@ int dc_plan_stats(dc_plan* plan, int64_t* decisions, int64_t* host_rankings,
 int dc_io_stats(dc_t* dc, int64_t* h2d_bytes, int64_t* d2h_bytes);
 void dc_plan_destroy(dc_plan* plan);
 
+/* --- serving: continuous batching over resident data centers -----------
+ * A server owns no data center; it drives n of them (created with dc_create,
+ * each preferably on its own CUDA stream so that launches for different data
+ * centers overlap).  dc_server_replay runs, on the calling thread, a timed
+ * sequence of arrivals: event i happens t_arrival_s[i] seconds after the
+ * start (non-decreasing) at data center inst[i]; kind[i] = 0 submits
+ * reqs[i], kind[i] = 1 is the departure of the request of event
+ * release_of[i] (an earlier kind-0 event of the same data center).  Arrived
+ * events are admitted in arrival order while the device footprint of
+ * admitted, unfinished requests stays within admit_bytes (a request larger
+ * than the budget is admitted alone); admitted events of a data center are
+ * scheduled in arrival order (FCFS, results identical to dc_schedule of the
+ * same sequence).  Whenever data centers with admitted work are idle, one
+ * batched launch covers all of them, while earlier launches for other data
+ * centers may still run (continuous batching).  max_requests_per_launch = 1
+ * instead runs one request per launch, one launch at a time (the plain
+ * scheduler).  Outputs per event: latency_s[i] (completion seen by the host
+ * minus arrival; kind 0 only) and req_id[i] (the id for dc_query on that data
+ * center; kind 0 only).  Results stay queryable with dc_query afterwards. */
+typedef struct dc_server dc_server;
+typedef struct {
+  int64_t launches;            /* launches issued */
+  int64_t requests;            /* requests completed */
+  int64_t decisions;           /* their pod decisions */
+  int64_t host_rankings;       /* their decisions x hosts */
+  int64_t peak_admitted_bytes; /* largest footprint of admitted, unfinished requests */
+  double wall_s;               /* replay duration */
+} dc_server_stats;
+
+int dc_server_create(dc_t* const* dcs, int32_t n, int64_t admit_bytes,
+                     int32_t max_requests_per_launch, dc_server** out);
+int dc_server_replay(dc_server* srv, int32_t n_events, const double* t_arrival_s,
+                     const int32_t* inst, const int32_t* kind, const dc_request* reqs,
+                     const int32_t* release_of, double* latency_s, int64_t* req_id,
+                     dc_server_stats* stats);
+void dc_server_destroy(dc_server* srv);
+
 /* Human-readable text of an error code (static storage). */
 const char* dc_strerror(int code);
 

@@ -1346,8 +1346,19 @@ __global__ void __launch_bounds__(B, 1) k_schedule(const InstDev* __restrict__ i
       schedule_request<B, HPT>(s, I, r);
     }
     __syncthreads();
+    if (I.progress && threadIdx.x == 0) {
+      __threadfence_system();
+      *reinterpret_cast<volatile int32_t*>(I.progress) = op + 1;
+    }
   }
   store_instance<B>(s, I);
+  if (I.progress) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence_system();
+      *reinterpret_cast<volatile int32_t*>(I.progress) = I.n_ops + 1;
+    }
+  }
 }
 
 // What-if ranking of pod `g` of request `r` with the given host_of, no

@@ -105,6 +105,10 @@ struct InstDev {
   unsigned long long* dx_inv;
   double* dx_pg;
   const unsigned long long* recip;
+  // optional: host-mapped progress word of this data center, written after
+  // every operation (operations done) and, once the block has stored the
+  // state back, set to n_ops + 1 (system-scope release)
+  int32_t* progress;
   int32_t* err;       // [1] 0 or a DC_E_* code
   // [3] pod decisions, host rankings (accumulated), launch start clock (min)
   unsigned long long* counters;

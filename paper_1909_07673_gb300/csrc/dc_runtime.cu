@@ -158,6 +158,9 @@ struct dc_t {
   // (cm[H], ctr[H], link slots) in this global scratch
   bool state_global = false;
   int32_t* d_gstate = nullptr;
+  // progress word in host-mapped memory (device pointer), set while a
+  // serving loop drives this data center; null otherwise
+  int32_t* progress_slot = nullptr;
   // host request store (pinned): per-container and per-link records in pod
   // order and the per-pod ranges (see ReqRec)
   PinnedVec<int4> c_lay, e_lay;
@@ -217,6 +220,7 @@ struct dc_plan {
   cudaGraphExec_t exec = nullptr;
   int64_t launch_id = 0;
   std::vector<size_t> req_begin, req_end;  // per dc: requests scheduled by this plan
+  std::vector<int32_t> n_ops;              // per dc: operations of this plan
   bool launched = false;
 };
 
@@ -428,6 +432,7 @@ InstDev make_desc(dc_t* d, const int32_t* d_ops, int n_ops, unsigned long long* 
   I.recip = d->d_recip;
   I.state_global = d->state_global ? 1 : 0;
   I.gstate = d->d_gstate;
+  I.progress = d->progress_slot;
   I.err = d->d_err;
   I.counters = counters;
   return I;
@@ -472,34 +477,39 @@ void destroy_plan_resources(dc_plan* p) {
   if (p->d_counters) cudaFreeAsync(p->d_counters, p->home);
 }
 
+// D2H of one data center's results of a plan into its pinned mirrors
+// (stream-ordered on `st`).
+int enqueue_collect_one(dc_plan* p, size_t i, cudaStream_t st) {
+  dc_t* d = p->dcs[i];
+  const size_t r0 = p->req_begin[i], r1 = p->req_end[i];
+  if (d->reqs.n == 0) return DC_OK;
+  // status of every request (releases change earlier ones)
+  DC_CUDA(cudaMemcpyAsync(d->m_status.p, d->o_status.p, d->reqs.n * 4, cudaMemcpyDeviceToHost, st));
+  if (r1 <= r0) return DC_OK;
+  const ReqRec a = d->reqs.p[r0], b = d->reqs.p[r1 - 1];
+  const int64_t c0 = a.c_off, c1 = b.c_off + b.n_c, e0 = a.e_off, e1 = b.e_off + b.n_e;
+  const int64_t p0 = a.p_off, p1 = b.p_off + b.n_p;
+  if (c1 > c0) {
+    DC_CUDA(cudaMemcpyAsync(d->m_host.p + c0, d->o_host.p + c0, (c1 - c0) * 4, cudaMemcpyDeviceToHost, st));
+    DC_CUDA(cudaMemcpyAsync(d->m_cpu.p + c0, d->o_cpu.p + c0, (c1 - c0) * 4, cudaMemcpyDeviceToHost, st));
+    DC_CUDA(cudaMemcpyAsync(d->m_mem.p + c0, d->o_mem.p + c0, (c1 - c0) * 4, cudaMemcpyDeviceToHost, st));
+  }
+  if (e1 > e0) {
+    DC_CUDA(cudaMemcpyAsync(d->m_bw.p + e0, d->o_bw.p + e0, (e1 - e0) * 4, cudaMemcpyDeviceToHost, st));
+    DC_CUDA(cudaMemcpyAsync(d->m_path.p + 6 * e0, d->o_path.p + 6 * e0, (e1 - e0) * 24, cudaMemcpyDeviceToHost, st));
+  }
+  if (p1 > p0)
+    DC_CUDA(cudaMemcpyAsync(d->m_score.p + p0, d->o_score.p + p0, (p1 - p0) * 8, cudaMemcpyDeviceToHost, st));
+  DC_CUDA(cudaMemcpyAsync(d->m_ndec.p + r0, d->o_ndec.p + r0, (r1 - r0) * 4, cudaMemcpyDeviceToHost, st));
+  DC_CUDA(cudaMemcpyAsync(d->m_tdone.p + r0, d->o_tdone.p + r0, (r1 - r0) * 8, cudaMemcpyDeviceToHost, st));
+  d->d2h_bytes += (c1 - c0) * 12 + (e1 - e0) * 28 + (p1 - p0) * 8 + (int64_t)(r1 - r0) * 12 +
+                  (int64_t)d->reqs.n * 4;
+  return DC_OK;
+}
+
 // D2H of a plan's results into the instances' pinned mirrors (stream-ordered).
 int enqueue_collect(dc_plan* p, cudaStream_t st) {
-  for (size_t i = 0; i < p->dcs.size(); ++i) {
-    dc_t* d = p->dcs[i];
-    const size_t r0 = p->req_begin[i], r1 = p->req_end[i];
-    if (d->reqs.n == 0) continue;
-    // status of every request (releases change earlier ones)
-    DC_CUDA(cudaMemcpyAsync(d->m_status.p, d->o_status.p, d->reqs.n * 4, cudaMemcpyDeviceToHost, st));
-    if (r1 <= r0) continue;
-    const ReqRec a = d->reqs.p[r0], b = d->reqs.p[r1 - 1];
-    const int64_t c0 = a.c_off, c1 = b.c_off + b.n_c, e0 = a.e_off, e1 = b.e_off + b.n_e;
-    const int64_t p0 = a.p_off, p1 = b.p_off + b.n_p;
-    if (c1 > c0) {
-      DC_CUDA(cudaMemcpyAsync(d->m_host.p + c0, d->o_host.p + c0, (c1 - c0) * 4, cudaMemcpyDeviceToHost, st));
-      DC_CUDA(cudaMemcpyAsync(d->m_cpu.p + c0, d->o_cpu.p + c0, (c1 - c0) * 4, cudaMemcpyDeviceToHost, st));
-      DC_CUDA(cudaMemcpyAsync(d->m_mem.p + c0, d->o_mem.p + c0, (c1 - c0) * 4, cudaMemcpyDeviceToHost, st));
-    }
-    if (e1 > e0) {
-      DC_CUDA(cudaMemcpyAsync(d->m_bw.p + e0, d->o_bw.p + e0, (e1 - e0) * 4, cudaMemcpyDeviceToHost, st));
-      DC_CUDA(cudaMemcpyAsync(d->m_path.p + 6 * e0, d->o_path.p + 6 * e0, (e1 - e0) * 24, cudaMemcpyDeviceToHost, st));
-    }
-    if (p1 > p0)
-      DC_CUDA(cudaMemcpyAsync(d->m_score.p + p0, d->o_score.p + p0, (p1 - p0) * 8, cudaMemcpyDeviceToHost, st));
-    DC_CUDA(cudaMemcpyAsync(d->m_ndec.p + r0, d->o_ndec.p + r0, (r1 - r0) * 4, cudaMemcpyDeviceToHost, st));
-    DC_CUDA(cudaMemcpyAsync(d->m_tdone.p + r0, d->o_tdone.p + r0, (r1 - r0) * 8, cudaMemcpyDeviceToHost, st));
-    d->d2h_bytes += (c1 - c0) * 12 + (e1 - e0) * 28 + (p1 - p0) * 8 + (int64_t)(r1 - r0) * 12 +
-                    (int64_t)d->reqs.n * 4;
-  }
+  for (size_t i = 0; i < p->dcs.size(); ++i) DC_TRY(enqueue_collect_one(p, i, st));
   return DC_OK;
 }
 
@@ -786,6 +796,7 @@ int dc_plan_create(dc_t* const* dcs, int32_t n, int32_t flags, dc_plan** out) {
     if (re <= rb) rb = re = 0;
     p->req_begin.push_back(rb);
     p->req_end.push_back(re);
+    p->n_ops.push_back((int32_t)(op1[i] - op0[i]));
     d->ops_claimed = op1[i];
     p->gens.push_back(d->gen);
   }
@@ -1246,4 +1257,343 @@ extern "C" int dc_rank_hosts_static(dc_t* d, const dc_request* q, int32_t pod,
   DC_CUDA(cudaMemcpyAsync(&nviable, base + L.nv, 4, cudaMemcpyDeviceToHost, st));
   DC_CUDA(cudaStreamSynchronize(st));
   return nviable;
+}
+
+// ---------------------------------------------------------------------------
+// Serving: continuous batching over resident data centers (dc_server_*).
+//
+// Each data center of the server gets one progress word in pinned host memory
+// mapped into the device; the scheduling kernel publishes, per data center,
+// the number of operations done and finally a "state stored" marker.  The
+// serving loop therefore sees requests complete while the launch that holds
+// them is still running, copies a finished data center's results on that data
+// center's own stream and puts the data center into the next launch at once,
+// independently of the other data centers of its launch.
+#include <chrono>
+#include <deque>
+#include <thread>
+
+struct dc_server {
+  std::vector<dc_t*> dcs;
+  int64_t admit_bytes = 0;
+  int32_t max_per_launch = 0;
+  int32_t* h_prog = nullptr;  // [n] host-mapped progress words
+  int32_t* d_prog = nullptr;
+  std::vector<cudaStream_t> pool;  // launch streams (one per running launch)
+};
+
+namespace {
+
+// device footprint of one request: inputs in the kernels' layout, outputs,
+// per-pod ranges and scores, request record and status words
+int64_t request_device_bytes(const dc_request* q) {
+  int32_t P = 0;
+  for (int32_t i = 0; i < q->n_containers; ++i) P = std::max(P, q->pod[i] + 1);
+  return (int64_t)q->n_containers * (16 + 12) + (int64_t)q->n_edges * (16 + 4 + 24) +
+         (int64_t)(P + 1) * 8 + (int64_t)P * 8 + 64;
+}
+
+struct Flight {
+  dc_plan* plan = nullptr;
+  int32_t stream_slot = -1;                 // launch stream of the server's pool
+  std::vector<int32_t> srv_idx;             // per plan dc: index in the server
+  std::vector<std::vector<int32_t>> evs;    // per plan dc: events in operation order
+  std::vector<int32_t> seen;                // per plan dc: operations seen done
+  std::vector<cudaEvent_t> collect_ev;      // per plan dc: results copied
+  std::vector<char> retired;                // per plan dc: released to the loop
+  int32_t live = 0;                         // plan dcs not retired yet
+};
+
+}  // namespace
+
+extern "C" int dc_server_create(dc_t* const* dcs, int32_t n, int64_t admit_bytes,
+                                int32_t max_requests_per_launch, dc_server** out) {
+  if (!dcs || n <= 0 || !out || admit_bytes <= 0 || max_requests_per_launch < 0) return DC_E_INVAL;
+  for (int32_t i = 0; i < n; ++i) {
+    if (!dcs[i] || dcs[i]->progress_slot) return DC_E_INVAL;  // one server per data center
+    for (int32_t j = 0; j < i; ++j)
+      if (dcs[j] == dcs[i]) return DC_E_INVAL;
+  }
+  dc_server* s = new (std::nothrow) dc_server();
+  if (!s) return DC_E_NOMEM;
+  if (cudaHostAlloc((void**)&s->h_prog, sizeof(int32_t) * n, cudaHostAllocMapped) != cudaSuccess) {
+    delete s;
+    return DC_E_NOMEM;
+  }
+  if (cudaHostGetDevicePointer((void**)&s->d_prog, s->h_prog, 0) != cudaSuccess) {
+    cudaFreeHost(s->h_prog);
+    delete s;
+    return DC_E_CUDA;
+  }
+  s->dcs.assign(dcs, dcs + n);
+  s->admit_bytes = admit_bytes;
+  s->max_per_launch = max_requests_per_launch;
+  for (int32_t i = 0; i < n; ++i) {
+    s->h_prog[i] = 0;
+    dcs[i]->progress_slot = s->d_prog + i;
+  }
+  *out = s;
+  return DC_OK;
+}
+
+namespace {
+// Grows an instance's host arenas and result mirrors once for `add_*` more
+// requests, containers, links and pods, so that no pinned reallocation
+// (whose free can synchronize the device) happens while launches run.
+int reserve_instance(dc_t* d, int64_t add_r, int64_t add_c, int64_t add_e, int64_t add_p) {
+  const size_t R = d->reqs.n + add_r, Cn = d->tot_c + add_c, En = d->tot_e + add_e;
+  const size_t L = d->tot_l + add_p + add_r, P = d->tot_p + add_p;
+  DC_TRY(d->c_lay.reserve(Cn));
+  DC_TRY(d->e_lay.reserve(En));
+  DC_TRY(d->p_coff.reserve(L));
+  DC_TRY(d->p_eoff.reserve(L));
+  DC_TRY(d->reqs.reserve(R));
+  DC_TRY(d->m_host.reserve(Cn));
+  DC_TRY(d->m_cpu.reserve(Cn));
+  DC_TRY(d->m_mem.reserve(Cn));
+  DC_TRY(d->m_bw.reserve(En));
+  DC_TRY(d->m_path.reserve(6 * En));
+  DC_TRY(d->m_score.reserve(P));
+  DC_TRY(d->m_status.reserve(R));
+  DC_TRY(d->m_ndec.reserve(R));
+  DC_TRY(d->m_tdone.reserve(R));
+  d->ops.reserve(d->ops.size() + 2 * add_r);
+  d->launch_of.reserve(R);
+  d->release_queued.reserve(R);
+  return DC_OK;
+}
+
+int server_stream(dc_server* s, std::vector<char>& used) {
+  for (size_t i = 0; i < s->pool.size(); ++i)
+    if (!used[i]) return (int)i;
+  cudaStream_t st;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) return -1;
+  s->pool.push_back(st);
+  used.push_back(0);
+  return (int)s->pool.size() - 1;
+}
+}  // namespace
+
+extern "C" void dc_server_destroy(dc_server* s) {
+  if (!s) return;
+  for (dc_t* d : s->dcs) {
+    cudaStreamSynchronize(d->stream);
+    d->progress_slot = nullptr;
+  }
+  for (auto st : s->pool) {
+    cudaStreamSynchronize(st);
+    cudaStreamDestroy(st);
+  }
+  if (s->h_prog) cudaFreeHost(s->h_prog);
+  delete s;
+}
+
+extern "C" int dc_server_replay(dc_server* s, int32_t n_ev, const double* t_arr, const int32_t* inst,
+                                const int32_t* kind, const dc_request* reqs,
+                                const int32_t* release_of, double* latency, int64_t* req_id,
+                                dc_server_stats* stats) {
+  if (!s || n_ev < 0 || (n_ev > 0 && (!t_arr || !inst || !kind || !reqs || !latency || !req_id)))
+    return DC_E_INVAL;
+  const int32_t N = (int32_t)s->dcs.size();
+  std::vector<int64_t> bytes(n_ev, 0);
+  int64_t total_req = 0;
+  for (int32_t e = 0; e < n_ev; ++e) {
+    if (inst[e] < 0 || inst[e] >= N || (kind[e] != 0 && kind[e] != 1)) return DC_E_INVAL;
+    if (e > 0 && t_arr[e] < t_arr[e - 1]) return DC_E_INVAL;
+    if (kind[e] == 1) {
+      if (!release_of) return DC_E_INVAL;
+      const int32_t r = release_of[e];
+      if (r < 0 || r >= e || kind[r] != 0 || inst[r] != inst[e]) return DC_E_INVAL;
+    } else {
+      bytes[e] = request_device_bytes(&reqs[e]);
+      ++total_req;
+    }
+    latency[e] = -1.0;
+    req_id[e] = -1;
+  }
+  {
+    std::vector<int64_t> ar(N, 0), ac(N, 0), ae(N, 0), ap(N, 0);
+    for (int32_t e = 0; e < n_ev; ++e) {
+      if (kind[e] != 0) continue;
+      const int32_t i = inst[e];
+      int32_t P = 0;
+      for (int32_t c = 0; c < reqs[e].n_containers; ++c) P = std::max(P, reqs[e].pod[c] + 1);
+      ar[i] += 1;
+      ac[i] += reqs[e].n_containers;
+      ae[i] += reqs[e].n_edges;
+      ap[i] += P;
+    }
+    for (int32_t i = 0; i < N; ++i) DC_TRY(reserve_instance(s->dcs[i], ar[i], ac[i], ae[i], ap[i]));
+  }
+  std::vector<std::deque<int32_t>> ready(N);
+  std::vector<char> busy(N, 0);
+  std::deque<int32_t> waitq;
+  std::vector<Flight> flights;
+  std::vector<char> stream_used(s->pool.size(), 0);
+  dc_server_stats st{};
+  int64_t admitted = 0;
+  int32_t next = 0;
+  int64_t done_req = 0;
+  int rc = DC_OK;
+  const auto t0 = std::chrono::steady_clock::now();
+  auto elapsed = [&]() {
+    return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  };
+  // moves the ready events of data center i (up to `limit` requests, 0 = all)
+  // into its FCFS queue
+  auto submit_ready = [&](int32_t i, int32_t limit, std::vector<int32_t>* evs) -> int {
+    dc_t* d = s->dcs[i];
+    int32_t nreq = 0;
+    while (!ready[i].empty() && (limit == 0 || nreq < limit)) {
+      const int32_t e = ready[i].front();
+      ready[i].pop_front();
+      if (kind[e] == 0) {
+        int64_t rid = -1;
+        DC_TRY(dc_submit_request(d, &reqs[e], &rid));
+        req_id[e] = rid;
+        ++nreq;
+      } else {
+        DC_TRY(dc_release(d, req_id[release_of[e]]));
+      }
+      evs->push_back(e);
+    }
+    return DC_OK;
+  };
+  while (rc == DC_OK && (done_req < total_req || next < n_ev || !flights.empty())) {
+    bool progress = false;
+    while (next < n_ev && t_arr[next] <= elapsed()) waitq.push_back(next++);
+    // admission in arrival order within the device-memory budget
+    while (!waitq.empty()) {
+      const int32_t e = waitq.front();
+      if (kind[e] == 0 && admitted > 0 && admitted + bytes[e] > s->admit_bytes) break;
+      admitted += bytes[e];
+      st.peak_admitted_bytes = std::max(st.peak_admitted_bytes, admitted);
+      ready[inst[e]].push_back(e);
+      waitq.pop_front();
+      progress = true;
+    }
+    // progress of running launches, per data center
+    for (size_t f = 0; f < flights.size() && rc == DC_OK;) {
+      Flight& fl = flights[f];
+      dc_plan* p = fl.plan;
+      for (size_t j = 0; j < p->dcs.size() && rc == DC_OK; ++j) {
+        if (fl.retired[j]) continue;
+        const int32_t i = fl.srv_idx[j];
+        const int32_t cnt = reinterpret_cast<volatile int32_t*>(s->h_prog)[i];
+        const int32_t nops = p->n_ops[j];
+        if (fl.seen[j] < std::min(cnt, nops)) {
+          const double t = elapsed();
+          while (fl.seen[j] < std::min(cnt, nops)) {
+            const int32_t e = fl.evs[j][fl.seen[j]++];
+            if (kind[e] == 0) latency[e] = t - t_arr[e];
+          }
+          progress = true;
+        }
+        if (cnt == nops + 1 && !fl.collect_ev[j]) {
+          dc_t* d = p->dcs[j];
+          rc = enqueue_collect_one(p, j, d->stream);
+          if (rc == DC_OK) rc = cuda_rc(cudaEventCreateWithFlags(&fl.collect_ev[j], cudaEventDisableTiming));
+          if (rc == DC_OK) rc = cuda_rc(cudaEventRecord(fl.collect_ev[j], d->stream));
+          progress = true;
+        }
+        if (rc == DC_OK && fl.collect_ev[j]) {
+          const cudaError_t q = cudaEventQuery(fl.collect_ev[j]);
+          if (q == cudaErrorNotReady) continue;
+          if (q != cudaSuccess) {
+            rc = DC_E_CUDA;
+            break;
+          }
+          dc_t* d = p->dcs[j];
+          const int64_t id = d->next_launch++;
+          for (size_t r = p->req_begin[j]; r < p->req_end[j]; ++r) d->launch_of[r] = id;
+          d->collected_launch = std::max(d->collected_launch, id);
+          for (int32_t e : fl.evs[j]) {
+            if (kind[e] != 0) continue;
+            admitted -= bytes[e];
+            ++done_req;
+            const int32_t nd = d->m_ndec.p[req_id[e]];
+            st.decisions += nd;
+            st.host_rankings += (int64_t)nd * d->H;
+          }
+          cudaEventDestroy(fl.collect_ev[j]);
+          fl.collect_ev[j] = nullptr;
+          fl.retired[j] = 1;
+          busy[i] = 0;
+          fl.live -= 1;
+          progress = true;
+        }
+      }
+      if (rc == DC_OK && fl.live == 0 && cudaEventQuery(p->done_ev) == cudaSuccess) {
+        stream_used[fl.stream_slot] = 0;
+        destroy_plan_resources(p);
+        delete p;
+        flights.erase(flights.begin() + f);
+        progress = true;
+      } else {
+        ++f;
+      }
+    }
+    if (rc != DC_OK) break;
+    // launches
+    std::vector<int32_t> group;
+    if (s->max_per_launch == 1) {
+      if (flights.empty()) {
+        int32_t best = -1;
+        for (int32_t i = 0; i < N; ++i)
+          if (!ready[i].empty() && (best < 0 || ready[i].front() < ready[best].front())) best = i;
+        if (best >= 0) group.push_back(best);
+      }
+    } else {
+      for (int32_t i = 0; i < N; ++i)
+        if (!busy[i] && !ready[i].empty()) group.push_back(i);
+    }
+    if (!group.empty()) {
+      Flight fl;
+      std::vector<dc_t*> dl;
+      for (int32_t i : group) {
+        fl.srv_idx.push_back(i);
+        fl.evs.emplace_back();
+        rc = submit_ready(i, s->max_per_launch == 1 ? 1 : s->max_per_launch, &fl.evs.back());
+        if (rc != DC_OK) break;
+        s->h_prog[i] = 0;
+        dl.push_back(s->dcs[i]);
+      }
+      if (rc == DC_OK) rc = dc_plan_create(dl.data(), (int32_t)dl.size(), 0, &fl.plan);
+      if (rc == DC_OK) {
+        fl.stream_slot = server_stream(s, stream_used);
+        if (fl.stream_slot < 0) rc = DC_E_CUDA;
+      }
+      if (rc == DC_OK) rc = dc_plan_launch(fl.plan, s->pool[fl.stream_slot]);
+      if (rc == DC_OK) stream_used[fl.stream_slot] = 1;
+      if (rc == DC_OK) {
+        fl.seen.assign(group.size(), 0);
+        fl.collect_ev.assign(group.size(), nullptr);
+        fl.retired.assign(group.size(), 0);
+        fl.live = (int32_t)group.size();
+        for (int32_t i : group) busy[i] = 1;
+        flights.push_back(std::move(fl));
+        ++st.launches;
+        progress = true;
+      }
+    }
+    if (!progress) {
+      if (flights.empty() && next < n_ev && waitq.empty()) {
+        const double wait = t_arr[next] - elapsed();
+        if (wait > 200e-6) std::this_thread::sleep_for(std::chrono::duration<double>(wait - 100e-6));
+      } else {
+        std::this_thread::yield();
+      }
+    }
+  }
+  for (auto& f : flights) {  // only after an error
+    cudaEventSynchronize(f.plan->done_ev);
+    for (auto ev : f.collect_ev)
+      if (ev) cudaEventDestroy(ev);
+    destroy_plan_resources(f.plan);
+    delete f.plan;
+  }
+  st.requests = done_req;
+  st.wall_s = elapsed();
+  if (stats) *stats = st;
+  return rc;
 }

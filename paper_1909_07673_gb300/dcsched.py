@@ -54,6 +54,12 @@ class _Result(C.Structure):
                 ("pod_score", _f64p), ("done_ns", C.c_int64)]
 
 
+class _ServerStats(C.Structure):
+    _fields_ = [("launches", C.c_int64), ("requests", C.c_int64), ("decisions", C.c_int64),
+                ("host_rankings", C.c_int64), ("peak_admitted_bytes", C.c_int64),
+                ("wall_s", C.c_double)]
+
+
 _lib = None
 
 
@@ -82,6 +88,13 @@ def lib():
         L.dc_rank_hosts_static.argtypes = [C.c_void_p, C.POINTER(_Request), C.c_int32, _i32p,
                                            _i32p, _f32p, _f64p, _i32p]
         L.dc_reset.argtypes = [C.c_void_p]
+        L.dc_server_create.argtypes = [C.POINTER(C.c_void_p), C.c_int32, C.c_int64, C.c_int32,
+                                       C.POINTER(C.c_void_p)]
+        L.dc_server_replay.argtypes = [C.c_void_p, C.c_int32, _f64p, _i32p, _i32p,
+                                       C.POINTER(_Request), _i32p, _f64p, _i64p,
+                                       C.POINTER(_ServerStats)]
+        L.dc_server_destroy.argtypes = [C.c_void_p]
+        L.dc_server_destroy.restype = None
         L.dc_plan_create.argtypes = [C.POINTER(C.c_void_p), C.c_int32, C.c_int32,
                                      C.POINTER(C.c_void_p)]
         L.dc_plan_launch.argtypes = [C.c_void_p, C.c_void_p]
@@ -273,6 +286,52 @@ class Plan:
     def close(self):
         if getattr(self, "h", None) and _lib is not None:
             _lib.dc_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+
+class Server:
+    """Continuous-batching serving loop over resident data centers (dc_server)."""
+
+    def __init__(self, dcs: Sequence[DataCenter], admit_bytes: int = 1 << 30,
+                 max_requests_per_launch: int = 0):
+        self.dcs = list(dcs)
+        h = C.c_void_p()
+        _check(lib().dc_server_create(_handles(self.dcs), len(self.dcs), admit_bytes,
+                                      max_requests_per_launch, C.byref(h)), "dc_server_create")
+        self.h = h
+
+    def replay(self, t, inst, kind, reqs, release_of):
+        """Replays timed events (see dc_server_replay); reqs[i] is a request
+        dict for kind-0 events (None otherwise).  Returns (latency_s,
+        req_id, stats dict).  The request ids are registered with the data
+        centers' bindings so that DataCenter.query works afterwards."""
+        n = len(t)
+        t = np.ascontiguousarray(t, np.float64)
+        inst = np.ascontiguousarray(inst, np.int32)
+        kind = np.ascontiguousarray(kind, np.int32)
+        rel = np.ascontiguousarray(release_of, np.int32)
+        keep = [(_Req(q) if q is not None else None) for q in reqs]
+        arr = (_Request * max(1, n))(*[(r.s if r is not None else _Request()) for r in keep])
+        lat = np.zeros(n, np.float64)
+        rid = np.zeros(n, np.int64)
+        st = _ServerStats()
+        _check(lib().dc_server_replay(self.h, n, _p(t, _f64p), _p(inst, _i32p), _p(kind, _i32p),
+                                      arr, _p(rel, _i32p), _p(lat, _f64p), _p(rid, _i64p),
+                                      C.byref(st)), "dc_server_replay")
+        for e in range(n):
+            if kind[e] == 0:
+                d = self.dcs[inst[e]]
+                assert rid[e] == len(d._reqs)
+                d._reqs.append(keep[e])
+        stats = {f: getattr(st, f) for f, _ in _ServerStats._fields_}
+        return lat, rid, stats
+
+    def close(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.dc_server_destroy(self.h)
             self.h = None
 
     def __del__(self):

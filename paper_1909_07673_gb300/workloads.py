@@ -400,4 +400,32 @@ def serving(seed: int = 3, method: int = TOPSIS, pair_rule: int = RATIO, scheme:
     return Workload("serving", insts, np.asarray(times), inst_of.astype(np.int64), local)
 
 
+def serving_events(wl: Workload):
+    """Flattens a serving workload into one timed event list: each arrival
+    (time, instance, kind 0, request index within the instance) followed by the
+    departures its instance's FCFS stream places right after it (kind 1, with
+    the event index of the departing request).  Returns arrays
+    (t, inst, kind, local, release_of)."""
+    t, inst, kind, local, rel = [], [], [], [], []
+    ev_of = {}  # (instance, local request) -> event index
+    pending = [dict() for _ in wl.instances]  # per instance: arrival j -> releases after it
+    for i, ins in enumerate(wl.instances):
+        last = None
+        for k, r in ins.ops:
+            if k == 0:
+                last = r
+            else:
+                pending[i].setdefault(last, []).append(r)
+    for g in range(len(wl.arrival_s)):
+        i, j = int(wl.arrival_inst[g]), int(wl.arrival_local[g])
+        ev_of[(i, j)] = len(t)
+        t.append(float(wl.arrival_s[g])); inst.append(i); kind.append(0); local.append(j)
+        rel.append(-1)
+        for r in pending[i].get(j, []):
+            t.append(float(wl.arrival_s[g])); inst.append(i); kind.append(1); local.append(r)
+            rel.append(ev_of[(i, r)])
+    return (np.asarray(t, np.float64), np.asarray(inst, np.int32), np.asarray(kind, np.int32),
+            np.asarray(local, np.int32), np.asarray(rel, np.int32))
+
+
 CONFIGS = {"small": small, "k16": k16, "k48": k48, "serving": serving, "batched": batched}
