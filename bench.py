@@ -13,8 +13,9 @@ Printed (rank 0, one JSON line): host-rankings/s of the whole job (pod
 decisions x hosts ranked per decision), requests/s, p50/p99 request
 completion latency inside the batched launch, the same work scheduled one
 request per launch, the end-to-end rate through the C-ABI with host buffers,
-the roofline of the scheduling kernel and the FP64 oracle timed on the
-host's cores.
+the roofline of the scheduling kernel, the FP64 oracle timed on the host's
+cores, and a serving replay (timed arrivals and departures through the
+continuous-batching server, p50/p99 latency, against one request per launch).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -53,6 +54,11 @@ def parse():
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--serving-events", type=int, default=0,
+                    help="serving replay: leading timed events to replay (0 = all)")
+    ap.add_argument("--plain-events", type=int, default=3000,
+                    help="serving replay one request per launch: leading events")
+    ap.add_argument("--no-serving", action="store_true")
     return ap.parse_args()
 
 
@@ -77,33 +83,50 @@ def config_dict(args, wl, world):
 
 # ----------------------------------------------------------------- oracle (CPU)
 
-def oracle_sample(wl, seconds):
-    """Runs the FP64 oracle (single thread) over leading requests of a
-    rotating set of instances until `seconds` pass; returns
-    (host_rankings, wall_s, description)."""
+def oracle_sample(wl, seconds, threads=1):
+    """Runs the FP64 oracle over the first requests (2 on one thread, 8 on
+    several) of instances taken in order (each thread takes the next instance; instances are independent)
+    until `seconds` pass; returns (host_rankings, wall_s, description,
+    requests, threads).  The oracle's C calls release the GIL, so the
+    threads run on separate cores."""
+    import concurrent.futures as cf
     import oracle as O
 
+    O.build_oracle()
+    per_inst = 2 if threads == 1 else 8  # requests per instance
     t0 = time.perf_counter()
-    hr = 0
-    reqs = 0
-    used = []
-    i = 0
-    # one instance of each size first, then more, 2 requests at a time
-    while time.perf_counter() - t0 < seconds and i < len(wl.instances):
-        inst = wl.instances[i]
-        dc = O.OracleDC.from_instance(inst)
-        r = 0
-        while r < inst.reqs.n and time.perf_counter() - t0 < seconds and r < 2:
-            out = dc.schedule(inst.reqs.request(r))
-            hr += out["n_decisions"] * inst.hosts
-            reqs += 1
-            r += 1
-        used.append((inst.k, r))
-        i += 1
+    lock = threading.Lock()
+    nxt = [0]
+    tot = {"hr": 0, "reqs": 0, "inst": 0, "ks": set()}
+
+    def worker():
+        while time.perf_counter() - t0 < seconds:
+            with lock:
+                i = nxt[0]
+                nxt[0] += 1
+            if i >= len(wl.instances):
+                return
+            inst = wl.instances[i]
+            dc = O.OracleDC.from_instance(inst)
+            hr = r = 0
+            while r < min(per_inst, inst.reqs.n) and time.perf_counter() - t0 < seconds:
+                out = dc.schedule(inst.reqs.request(r))
+                hr += out["n_decisions"] * inst.hosts
+                r += 1
+            with lock:
+                tot["hr"] += hr
+                tot["reqs"] += r
+                tot["inst"] += 1
+                tot["ks"].add(inst.k)
+
+    with cf.ThreadPoolExecutor(threads) as ex:
+        for f in [ex.submit(worker) for _ in range(threads)]:
+            f.result()
     wall = time.perf_counter() - t0
-    desc = "oracle.c single thread, first %s requests of %d instances (k=%s), %.1f s" % (
-        "1-2", len(used), sorted(set(k for k, _ in used)), wall)
-    return hr, wall, desc, reqs
+    desc = ("oracle.c (FP64), %d thread(s) over independent instances: first 1-%d requests of "
+            "%d instances (k=%s), %.1f s" % (threads, per_inst, tot["inst"], sorted(tot["ks"]),
+                                             wall))
+    return tot["hr"], wall, desc, tot["reqs"], threads
 
 
 def run_reference(args):
@@ -117,8 +140,9 @@ def run_reference(args):
     wl = workload(args, 0)
     per = max(1.0, args.cpu_seconds / max(1, args.steps))
     times, hrs = [], []
+    cores = os.cpu_count() or 1
     for s in range(args.warmup + args.steps):
-        hr, wall, desc, reqs = oracle_sample(wl, per)
+        hr, wall, desc, reqs, _ = oracle_sample(wl, per, cores)
         if s >= args.warmup:
             times.append(wall)
             hrs.append(hr)
@@ -129,8 +153,8 @@ def run_reference(args):
         "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": config_dict(args, wl, 1),
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "each step: " + desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -195,6 +219,20 @@ class Clocks:
 
 # ----------------------------------------------------------------- helpers
 
+def reduce_over_ranks(dist, times, counts, device):
+    """Job-wide figures: the maximum of each time and the sum of each count
+    over all ranks (dist None: one rank)."""
+    import torch
+
+    if dist is None:
+        return [float(x) for x in times], [int(x) for x in counts]
+    t = torch.tensor([float(x) for x in times] + [0.0], dtype=torch.float64, device=device)
+    c = torch.tensor([int(x) for x in counts] + [0], dtype=torch.int64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return [float(x) for x in t.tolist()[:-1]], [int(x) for x in c.tolist()[:-1]]
+
+
 def measured_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -225,6 +263,49 @@ def ncu_traffic(host_rankings_per_launch):
     if t.get("source_hash") != kernel_source_hash():
         return None
     return t["dram_bytes"] / t["host_rankings"] * host_rankings_per_launch
+
+
+# ----------------------------------------------------------------- serving
+
+def run_serving(args, ds, torch):
+    """Replays the serving workload (64 k=16 data centers, Poisson arrivals
+    at 50k requests/s for 1 s, Zipf(1.1) over the data centers, 2-128
+    containers, exponential lifetimes) through dc_server_replay, with
+    continuous batching and, on a prefix, one request per launch."""
+    from paper_1909_07673_gb300 import workloads as W
+
+    wl = W.serving()
+    ev = W.serving_events(wl)
+
+    def replay(limit, per_launch):
+        t, inst, kind, local, rel = (x[:limit] if limit else x for x in ev)
+        reqs = [wl.instances[inst[e]].reqs.request(int(local[e])) if kind[e] == 0 else None
+                for e in range(len(t))]
+        dcs = [ds.DataCenter.from_instance(i, stream=torch.cuda.Stream()) for i in wl.instances]
+        srv = ds.Server(dcs, admit_bytes=1 << 30, max_requests_per_launch=per_launch)
+        lat, rid, st = srv.replay(t, inst, kind, reqs, rel)
+        srv.close()
+        for d in dcs:
+            d.close()
+        L = np.sort(lat[kind == 0]) * 1e3
+        return {"events": int(len(t)), "requests": int(st["requests"]),
+                "arrival_span_s": float(t[-1]), "wall_s": st["wall_s"],
+                "requests_per_s": st["requests"] / st["wall_s"],
+                "host_rankings_per_s": st["host_rankings"] / st["wall_s"],
+                "launches": int(st["launches"]),
+                "latency_ms": {"p50": float(L[len(L) // 2]), "p99": float(L[int(len(L) * 0.99)])}}
+
+    batched = replay(args.serving_events, 0)
+    plain = replay(args.plain_events, 1)
+    return {
+        "workload": "64 k=16 data centers (0-70 %% pre-load), Poisson %d requests/s for 1 s, "
+                    "Zipf(1.1) over data centers, 2-128 containers, lifetimes Exp(100 arrivals)"
+                    % 50000,
+        "latency": "arrival (replayed on the host clock) to completion seen by the host",
+        "continuous_batching": batched,
+        "plain_launch": dict(plain, note="one request per launch, one launch at a time, "
+                                         "first %d events" % plain["events"]),
+    }
 
 
 # ----------------------------------------------------------------- ours
@@ -288,10 +369,8 @@ def run_ours(args):
             st, nd, done = dc.status(r)
             lat.append((done - start_ns) * 1e-6)
             accepted += st == ds.ACCEPTED
-    t_max = torch.tensor([ms_step, ms_kernel], dtype=torch.float64, device="cuda")
-    if dist:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    ms_step, ms_kernel = float(t_max[0]), float(t_max[1])
+    (ms_step, ms_kernel), (hr_all, dec_all, req_all, acc_all) = reduce_over_ranks(
+        dist, [ms_step, ms_kernel], [hr, dec, n_req, accepted], "cuda")
 
     # one request per launch on a sample (one instance per size, 8 requests)
     plain_hr, plain_req, plain_s = 0, 0, 0.0
@@ -333,7 +412,8 @@ def run_ours(args):
     io1 = [dc.io_stats() for dc in dcs]
     h2d = sum(b[0] - a[0] for a, b in zip(io0, io1)) / args.e2e_steps
     d2h = sum(b[1] - a[1] for a, b in zip(io0, io1)) / args.e2e_steps
-    e2e_value = world * hr / statistics.mean(e2e_times)
+    (e2e_s,), _ = reduce_over_ranks(dist, [statistics.mean(e2e_times)], [], "cuda")
+    e2e_value = hr_all / e2e_s
 
     peak, peak_kind = measured_peak()
     achieved = hr * BYTES_PER_HOST_RANKING / (ms_kernel * 1e-3) / 1e9
@@ -342,18 +422,21 @@ def run_ours(args):
         if dist:
             dist.barrier()
         return 0
-    cpu_hr, cpu_s, cpu_desc, _ = oracle_sample(wl, args.cpu_seconds)
+    serving = None if args.no_serving else run_serving(args, ds, torch)
+    cpu_hr, cpu_s, cpu_desc, _, cpu_threads = oracle_sample(wl, args.cpu_seconds,
+                                                            os.cpu_count() or 1)
+    one_hr, one_s, one_desc, _, _ = oracle_sample(wl, max(2.0, args.cpu_seconds / 3), 1)
     lat.sort()
     line = {
-        "metric": METRIC, "value": world * hr / (ms_step * 1e-3), "unit": UNIT,
+        "metric": METRIC, "value": hr_all / (ms_step * 1e-3), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": config_dict(args, wl, world),
-        "host_rankings_per_step": world * hr, "decisions_per_step": world * dec,
-        "requests_per_s": world * n_req / (ms_step * 1e-3),
-        "decisions_per_s": world * dec / (ms_step * 1e-3),
-        "accepted_fraction": accepted / n_req,
+        "host_rankings_per_step": hr_all, "decisions_per_step": dec_all,
+        "requests_per_s": req_all / (ms_step * 1e-3),
+        "decisions_per_s": dec_all / (ms_step * 1e-3),
+        "accepted_fraction": acc_all / req_all,
         "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[int(len(lat) * 0.99)],
                        "note": "request completion time from the start of the batched launch"},
         "plain_launch": {"host_rankings_per_s": plain_hr / plain_s,
@@ -368,10 +451,13 @@ def run_ours(args):
                      "peak_kind": peak_kind + " (STREAM-style copy)",
                      "note": "16 B of host state per host ranking over the scheduling launch "
                              "(graph: state reset + one kernel per fat-tree size)"},
-        "cpu_baseline": {"value": cpu_hr / cpu_s, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": cpu_desc},
+        "cpu_baseline": {"value": cpu_hr / cpu_s, "unit": UNIT, "cores": cpu_threads,
+                         "kind": "oracle", "sample": cpu_desc,
+                         "single_thread": {"value": one_hr / one_s, "sample": one_desc}},
         "clocks": clk.summary(),
     }
+    if serving is not None:
+        line["serving"] = serving
     print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
