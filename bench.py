@@ -59,6 +59,12 @@ def parse():
     ap.add_argument("--plain-events", type=int, default=3000,
                     help="serving replay one request per launch: leading events")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch shapes (one block per data center)")
+    ap.add_argument("--tune-ops", type=int, default=20,
+                    help="operations per data center run in each autotuner trial")
+    ap.add_argument("--no-largest", action="store_true",
+                    help="skip the single k=48 data-center measurement")
     return ap.parse_args()
 
 
@@ -308,6 +314,53 @@ def run_serving(args, ds, torch):
     }
 
 
+# ----------------------------------------------------------------- largest fat-tree
+
+def run_largest(args, ds, torch, peak):
+    """One k=48 data center (27,648 hosts, 40 Gbps, 0-100 % pre-load), 200
+    requests of 64-512 containers in pods of 1-8, Pareto bandwidths, TOPSIS
+    over 6 criteria: a single sequential chain of pod decisions, scheduled
+    with the autotuned cluster shape (state-resetting launches)."""
+    from paper_1909_07673_gb300 import workloads as W
+
+    inst = W.k48().instances[0]
+    stream = torch.cuda.Stream()
+    dc = ds.load_instance(inst, stream=stream)
+    tuned = None if args.no_autotune else ds.autotune([dc], max_ops=8)
+    plan = ds.Plan([dc], ds.PLAN_RESET)
+    times = []
+    for rep in range(3):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        plan.launch(stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if rep > 0:
+            times.append(e0.elapsed_time(e1))
+    plan.collect()
+    dec, hr, nk, _ = plan.stats()
+    ms = statistics.mean(times)
+    block, ncta, _ = ds.get_launch(dc)
+    acc = sum(dc.status(r)[0] == ds.ACCEPTED for r in range(inst.reqs.n))
+    gbs = hr * BYTES_PER_HOST_RANKING / (ms * 1e-3) / 1e9
+    plan.close()
+    dc.close()
+    return {
+        "workload": "one k=48 fat-tree (27,648 hosts), 200 requests of 64-512 containers in "
+                    "pods of 1-8, TOPSIS, 6 criteria",
+        "host_rankings_per_s": hr / (ms * 1e-3), "decisions_per_s": dec / (ms * 1e-3),
+        "us_per_decision": ms * 1e3 / dec, "ms_per_launch": ms, "decisions": dec,
+        "accepted_requests": int(acc),
+        "launch_shape": {"block": block, "blocks_per_dc": ncta,
+                         "trials": tuned[0]["trials"] if tuned else 0},
+        "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                     "frac": gbs / peak,
+                     "note": "16 B of host state per host ranking; one data center is a "
+                             "sequential chain of decisions (latency-bound)"},
+    }
+
+
 # ----------------------------------------------------------------- ours
 
 def run_ours(args):
@@ -329,6 +382,7 @@ def run_ours(args):
     wl = workload(args, rank)
     stream = torch.cuda.Stream()
     dcs = [ds.load_instance(inst, stream=stream) for inst in wl.instances]
+    tuned = None if args.no_autotune else ds.autotune(dcs, max_ops=args.tune_ops)
     plan = ds.Plan(dcs, ds.PLAN_GRAPH | ds.PLAN_RESET)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
@@ -418,6 +472,7 @@ def run_ours(args):
     peak, peak_kind = measured_peak()
     achieved = hr * BYTES_PER_HOST_RANKING / (ms_kernel * 1e-3) / 1e9
     traffic = ncu_traffic(hr)
+    largest = None if args.no_largest else run_largest(args, ds, torch, peak)
     if rank != 0:
         if dist:
             dist.barrier()
@@ -427,12 +482,20 @@ def run_ours(args):
                                                             os.cpu_count() or 1)
     one_hr, one_s, one_desc, _, _ = oracle_sample(wl, max(2.0, args.cpu_seconds / 3), 1)
     lat.sort()
+    cfg = config_dict(args, wl, world)
+    if tuned is not None:
+        cfg["launch_shapes"] = [
+            {"k": e["k"], "block": e["block"], "blocks_per_dc": e["ncta"],
+             "default": [e["block0"], e["ncta0"]], "trials": e["trials"]} for e in tuned]
+        cfg["autotune"] = ("coordinate descent over launch shapes per fat-tree size, each "
+                           "trial a state-resetting launch of the first %d operations of every "
+                           "data center" % args.tune_ops)
     line = {
         "metric": METRIC, "value": hr_all / (ms_step * 1e-3), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
-        "config": config_dict(args, wl, world),
+        "config": cfg,
         "host_rankings_per_step": hr_all, "decisions_per_step": dec_all,
         "requests_per_s": req_all / (ms_step * 1e-3),
         "decisions_per_s": dec_all / (ms_step * 1e-3),
@@ -458,6 +521,8 @@ def run_ours(args):
     }
     if serving is not None:
         line["serving"] = serving
+    if largest is not None:
+        line["largest_fat_tree"] = largest
     print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

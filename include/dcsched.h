@@ -216,6 +216,55 @@ int dc_plan_stats(dc_plan* plan, int64_t* decisions, int64_t* host_rankings,
 int dc_io_stats(dc_t* dc, int64_t* h2d_bytes, int64_t* d2h_bytes);
 void dc_plan_destroy(dc_plan* plan);
 
+/* --- launch shapes --------------------------------------------------------
+ * No counterpart in the paper (a GPU launch parameter).  The scheduling
+ * kernel of a plan runs one thread block of `block` threads per data center
+ * or, with ncta > 1, one thread-block cluster of ncta blocks that splits the
+ * data center's pods (and their hosts and edge switches) between the blocks:
+ * each block ranks its own hosts, the column statistics and the argmax are
+ * combined across the cluster through distributed shared memory, and block
+ * 0 commits on the state, which then lives in global memory.  Placements,
+ * states and scores are identical for every shape.
+ *
+ * dc_set_launch records the shape for data centers of fat-tree size k with
+ * n_criteria criteria, method and pair_rule (ignored for TOPSIS); plans
+ * created afterwards (dc_plan_create, dc_schedule, servers) use it.  The
+ * table is process-wide; without an entry a data center keeps the shape
+ * dc_create chose.  block: 128, 256, 512 or 1024 with k^3/4 <= 32 * block;
+ * ncta: 1, or 2..16 dividing k with block >= 256 and not AHP DIFF.
+ * block = 0 removes the entry.  DC_E_INVAL for a shape that cannot run such
+ * a data center on the current device (shared memory, cluster residency).
+ * dc_get_launch reports the shape a plan created now would use for dc. */
+int dc_set_launch(int32_t k, int32_t n_criteria, int32_t method, int32_t pair_rule,
+                  int32_t block, int32_t ncta);
+int dc_get_launch(const dc_t* dc, int32_t* block, int32_t* ncta, int64_t* smem_bytes);
+
+/* --- autotuner --------------------------------------------------------------
+ * No counterpart in the paper.  dc_autotune chooses, for every kind of data
+ * center among dcs (k, criteria, method, pair rule), the launch shape that
+ * minimises the device time of the batched launch of the instances' queued
+ * operations, and records it with dc_set_launch.  Coordinate descent over
+ * the kinds, largest work (pods x hosts) first: every candidate shape of the
+ * kind (all valid blocks; clusters of 2..16 blocks with >= 256 hosts per
+ * block) is timed with CUDA events as a state-resetting launch of all n
+ * instances, best of two after a warm-up, the other kinds keeping their
+ * current shapes; a candidate replaces the current shape when it is at
+ * least 3 % faster.  Only the first max_ops operations of every instance
+ * run in a trial (0: all).  Blocking.  The instances' state and queues are
+ * as before the call (their device state is saved and restored).  Writes
+ * one entry per kind, up to max_out, and the number of kinds to *n_out. */
+typedef struct {
+  int32_t k, n_criteria, method, pair_rule;
+  int32_t block, ncta;    /* chosen shape */
+  int32_t block0, ncta0;  /* shape before tuning */
+  int32_t trials;         /* candidate shapes timed */
+  int32_t pad;
+  double ms;              /* launch time with the chosen shape (ms) */
+  double ms0;             /* launch time before this kind was tuned (ms) */
+} dc_tune_entry;
+int dc_autotune(dc_t* const* dcs, int32_t n, int32_t max_ops, dc_tune_entry* out,
+                int32_t max_out, int32_t* n_out);
+
 /* --- serving: continuous batching over resident data centers -----------
  * A server owns no data center; it drives n of them (created with dc_create,
  * each preferably on its own CUDA stream so that launches for different data

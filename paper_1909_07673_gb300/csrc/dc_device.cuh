@@ -58,6 +58,25 @@ namespace dcs {
 
 // ---------------------------------------------------------------- context
 
+// Partial results one block publishes to the other blocks of its cluster
+// (read through distributed shared memory after a cluster barrier).  Each
+// kind of exchange has its own fields, and consecutive uses of one field are
+// always separated by a barrier of another kind, so no field is rewritten
+// while another block may still read it.
+struct Xch {
+  long long S1[kMaxC], S2[kMaxC];  // column statistics over the block's hosts
+  int32_t mx[kMaxC], mn[kMaxC];
+  int32_t n;
+  int32_t flag;                    // tie certification: a tie with other criteria
+  float m1, m2;                    // block argmax (see Sel)
+  int32_t idx, cnt;
+  int32_t x[kMaxC];                // criteria of the block's leader
+  double s64;                      // FP64 band: best score, its host, criteria
+  int32_t idx64;
+  int32_t x64[kMaxC];
+  int32_t ok;                      // commit result (rank 0)
+};
+
 struct Ctx {
   // instance
   int32_t k, half, H, E, C, method, link_mbps;
@@ -100,6 +119,16 @@ struct Ctx {
   int32_t ndec;
   int32_t nvc;      // viable hosts counted by the AHP DIFF compaction
   double wscore;    // AHP DIFF: exact global priority of the winner
+  int32_t cnt1;     // hosts at the maximum FP32 score
+  int32_t full;     // certification needs the FP64 band
+  int32_t x1[kMaxC];  // criteria of the leader idx1
+  int32_t xw[kMaxC];  // criteria of the winner (its decision record)
+  // blocks sharing the data center (a thread-block cluster; 1 block: rank 0
+  // of 1): this block ranks the hosts [h0, h1) of pods [p0, p1) and builds
+  // their switch tables; block 0 alone writes the shared state and outputs
+  int32_t rank, ncta, p0, p1, h0, h1;
+  int32_t hof_smem;  // hof is this block's shared copy
+  Xch xs;
 };
 
 struct Sm {
@@ -119,6 +148,8 @@ struct Sm {
   int32_t *st_pc, *st_pe, *st_hof;
   int4* pel;
   int4* curc;  // [32] container records of the pod being placed
+  int32_t* xwarp;  // [B / 32][kMaxC] criteria of each warp's leader
+  int32_t *wg, *wm;  // [E] each: wide table passes (global-state data centers)
 };
 
 static __device__ __forceinline__ Sm carve(unsigned char* base, const InstDev& I, int B) {
@@ -154,6 +185,9 @@ static __device__ __forceinline__ Sm carve(unsigned char* base, const InstDev& I
   s.st_hof = reinterpret_cast<int32_t*>(base + L.st_hof);
   s.pel = reinterpret_cast<int4*>(base + L.pel);
   s.curc = reinterpret_cast<int4*>(base + L.curc);
+  s.xwarp = reinterpret_cast<int32_t*>(base + L.xwarp);
+  s.wg = reinterpret_cast<int32_t*>(base + L.wide);
+  s.wm = s.wg + E;
   return s;
 }
 
@@ -164,6 +198,30 @@ static __device__ __forceinline__ unsigned long long globaltimer_ns() {
   unsigned long long t;
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
   return t;
+}
+// thread-block cluster: rank of this block, cluster index, barrier with
+// release / acquire semantics at cluster scope (orders the global and shared
+// memory accesses of all blocks of the cluster), and the generic address of
+// a shared variable in another block of the cluster
+static __device__ __forceinline__ int cl_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return (int)r;
+}
+static __device__ __forceinline__ int cl_id() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return (int)r;
+}
+static __device__ __forceinline__ void cl_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;"
+               ::: "memory");
+}
+template <class T>
+static __device__ __forceinline__ const T* cl_map(const T* p, int rank) {
+  unsigned long long a;
+  asm volatile("mapa.u64 %0, %1, %2;" : "=l"(a) : "l"(p), "r"(rank));
+  return reinterpret_cast<const T*>(a);
 }
 static __device__ __forceinline__ int imin(int a, int b) { return a < b ? a : b; }
 static __device__ __forceinline__ int imax(int a, int b) { return a > b ? a : b; }
@@ -540,17 +598,20 @@ static __device__ void pod_clear_warp(const Sm& s) {
 // edge switch e to edge(v)) folded over the pod's placed neighbours v.
 // Lanes are grouped per pod (gs lanes, lane a of a group = aggregation a);
 // each lane computes max_c min(ac(p, a, c), ac(pod(v), a, c)) for its a and
-// the group shares the values by shuffles.  Ends with a barrier.
+// the group shares the values by shuffles.  Only the edge switches of this
+// block's pods [p0, p1) (gs divides 32, so groups never straddle warps).
+// Ends with a barrier.
 template <int B>
 static __device__ void build_tables(const Sm& s) {
   const Ctx& c = *s.c;
-  const int half = c.half, gs = c.gs, k = c.k;
+  const int half = c.half, gs = c.gs;
   const int lane = lane_id();
   const int gbase = lane & ~(gs - 1);
-  for (int t0 = threadIdx.x - lane; t0 < k * gs; t0 += B) {
+  const int tend = c.p1 * gs;
+  for (int t0 = c.p0 * gs + threadIdx.x - lane; t0 < tend; t0 += B) {
     const int t = t0 + lane;
     const int p = t / gs, a = t - p * gs;  // gs is a power of two
-    const bool active = t < k * gs && a < half;
+    const bool active = t < tend && a < half;
     const int e = p * half + a;
     Top2 tt = {kInf, -1, kInf}, sl = {kInf, -1, kInf};
     for (int i = 0; i < c.npe; ++i) {
@@ -558,10 +619,14 @@ static __device__ void build_tables(const Sm& s) {
       const int v = q.y, need = q.z;
       const int ev = div_half(c, v), pv = div_half(c, ev);
       int gm = -1;
-      if (active && p != pv)
+      if (active && p != pv) {
+        // independent loads: unrolled so that several are in flight
+#pragma unroll 8
         for (int cc = 0; cc < half; ++cc)
           gm = imax(gm, imin(s.lk[s_ac(c, p * half + a, cc)], s.lk[s_ac(c, pv * half + a, cc)]));
+      }
       int mid = -1;
+#pragma unroll 8
       for (int a2 = 0; a2 < half; ++a2) {
         const int g2 = __shfl_sync(0xffffffffu, gm, gbase + a2);
         if (active) {
@@ -585,8 +650,87 @@ static __device__ void build_tables(const Sm& s) {
   __syncthreads();
 }
 
-// a4: exact column statistics over the viable hosts and FP32 constants.
+// The same tables for a data center whose state lives in global memory,
+// in three block-wide passes per neighbour so that the loads of the link
+// residuals are spread over all threads (one level of memory latency per
+// pass) instead of forming per-lane chains:
+//   G[p][a] = max_c min(ac(p, a, c), ac(pod(v), a, c))   for p != pod(v)
+//   M[e]    = max_a min(ea(e, a), ea(edge(v), a) [, G[pod(e)][a]])
+//   T       = min(uplink(v), M[e]) (no switch link when e = edge(v)),
+// folded into the top-2 tables in neighbour order like build_tables.
+// Only this block's pods [p0, p1).  Ends with a barrier.
 template <int B>
+static __device__ void build_tables_wide(const Sm& s) {
+  const Ctx& c = *s.c;
+  const int half = c.half, tid = threadIdx.x;
+  const int np = c.p1 - c.p0, ne = np * half, nt = ne * half;
+  const int e0 = c.p0 * half;
+  for (int el = tid; el < ne; el += B) {
+    const int e = e0 + el;
+    s.T1[e] = kInf; s.T1h[e] = -1; s.T2[e] = kInf;
+    s.S1[e] = kInf; s.S1h[e] = -1; s.S2[e] = kInf;
+    s.wg[el] = -1;
+    s.wm[el] = -1;
+  }
+  __syncthreads();
+  for (int i = 0; i < c.npe; ++i) {
+    const int4 q = c.pel[i];
+    const int v = q.y, need = q.z;
+    const int ev = div_half(c, v), pv = div_half(c, ev);
+    // pass 1: (pod, aggregation, core) triples of this block; consecutive
+    // threads take consecutive aggregation switches (contiguous link slots,
+    // distinct maxima)
+    for (int t = tid; t < nt; t += B) {
+      const int cc = t / ne, pa = t - cc * ne;  // pa = pod-local * half + a
+      const int pl = div_half(c, pa), a = pa - pl * half;
+      const int p = c.p0 + pl;
+      if (p != pv)
+        atomicMax(&s.wg[pa], imin(s.lk[s_ac(c, p * half + a, cc)], s.lk[s_ac(c, pv * half + a, cc)]));
+    }
+    __syncthreads();
+    // pass 2: (edge switch, aggregation) pairs of this block, consecutive
+    // threads over consecutive edge switches
+    for (int t = tid; t < nt; t += B) {
+      const int a = t / ne, el = t - a * ne;
+      const int pl = div_half(c, el);
+      const int e = e0 + el;
+      int m = imin(s.lk[s_ea(c, e, a)], s.lk[s_ea(c, ev, a)]);
+      if (c.p0 + pl != pv) m = imin(m, s.wg[pl * half + a]);
+      atomicMax(&s.wm[el], m);
+    }
+    __syncthreads();
+    // pass 3: fold per edge switch (one thread per switch), reset the maxima
+    const int up = s.lk[v];
+    for (int el = tid; el < ne; el += B) {
+      const int e = e0 + el;
+      const int mid = e == ev ? kInf : s.wm[el];
+      const int T = imin(up, mid);
+      const Top2 tt = min2_combine(Top2{s.T1[e], s.T1h[e], s.T2[e]}, Top2{T, v, kInf});
+      const Top2 sl = min2_combine(Top2{s.S1[e], s.S1h[e], s.S2[e]}, Top2{T - need, v, kInf});
+      s.T1[e] = tt.v1; s.T1h[e] = tt.h1; s.T2[e] = tt.v2;
+      s.S1[e] = sl.v1; s.S1h[e] = sl.h1; s.S2[e] = sl.v2;
+      s.wg[el] = -1;
+      s.wm[el] = -1;
+    }
+    __syncthreads();
+  }
+}
+
+// Tables of this block's pods: the wide passes for a global state when the
+// block holds few pods (measured: up to 12), else the per-lane form.
+template <int B>
+static __device__ __forceinline__ void tables(const Sm& s, const InstDev& I) {
+  if (I.state_global && s.c->p1 - s.c->p0 <= 12)
+    build_tables_wide<B>(s);
+  else
+    build_tables<B>(s);
+}
+
+// a4: exact column statistics over the viable hosts and FP32 constants.
+// In a cluster every block reduces its own hosts, publishes the partial
+// statistics and then combines those of all blocks (exact integers, so all
+// blocks obtain the same values).
+template <int B, bool CL>
 static __device__ void column_stats(const Sm& s) {
   Ctx& c = *s.c;
   const int tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
@@ -598,7 +742,8 @@ static __device__ void column_stats(const Sm& s) {
   int mx[kMaxC], mn[kMaxC];
 #pragma unroll
   for (int v = 0; v < kMaxC; ++v) { s1[v] = 0; s2[v] = 0; mx[v] = INT_MIN; mn[v] = INT_MAX; }
-  for (int u = tid; u < c.H; u += B) {
+#pragma unroll 2
+  for (int u = c.h0 + tid; u < c.h1; u += B) {
     int32_t x[kMaxC];
     if (host_crit<B>(s, u, x)) {
       ++cnt;
@@ -651,6 +796,16 @@ static __device__ void column_stats(const Sm& s) {
     M = __reduce_max_sync(0xffffffffu, M);
     N = __reduce_min_sync(0xffffffffu, N);
     n = (int)__reduce_add_sync(0xffffffffu, (uint32_t)n);
+    if (CL) {
+      if (lane == 0) {
+        c.xs.S1[v] = a;
+        c.xs.S2[v] = b;
+        c.xs.mx[v] = M;
+        c.xs.mn[v] = N;
+        if (v == 0) c.xs.n = n;
+      }
+      continue;
+    }
     if (lane == 0) {
       c.S1[v] = a;
       c.S2[v] = b;
@@ -660,6 +815,37 @@ static __device__ void column_stats(const Sm& s) {
       // FP32 constants: q_v = W_v / sqrt(sum x^2); 1 / sum (x + 1)
       c.qf[v] = b > 0 ? __fmul_rn(c.Wf[v], __frsqrt_rn((float)b)) : 0.f;
       c.invTf[v] = __frcp_rn((float)(a + n));
+    }
+  }
+  if (CL) {
+    cl_sync();
+    for (int v = w; v < C; v += NW) {
+      long long a = 0, b = 0;
+      int M = INT_MIN, N = INT_MAX, n = 0;
+      if (lane < c.ncta) {
+        const Xch* R = cl_map(&c.xs, lane);
+        a = R->S1[v];
+        b = R->S2[v];
+        M = R->mx[v];
+        N = R->mn[v];
+        n = R->n;
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b += __shfl_xor_sync(0xffffffffu, b, o);
+      }
+      M = __reduce_max_sync(0xffffffffu, M);
+      N = __reduce_min_sync(0xffffffffu, N);
+      n = (int)__reduce_add_sync(0xffffffffu, (uint32_t)n);
+      if (lane == 0) {
+        c.S1[v] = a;
+        c.S2[v] = b;
+        c.mx[v] = M;
+        c.mn[v] = N;
+        if (v == 0) c.n = n;
+        c.qf[v] = b > 0 ? __fmul_rn(c.Wf[v], __frsqrt_rn((float)b)) : 0.f;
+        c.invTf[v] = __frcp_rn((float)(a + n));
+      }
     }
   }
   __syncthreads();
@@ -820,21 +1006,48 @@ static __device__ __forceinline__ float cand_score(const Sm& s, int u, int32_t* 
   return score32(*s.c, x);
 }
 
+// Criteria of the leader of a reduction: `ow` is the lane whose partial
+// holds the winning index (ballot of the lanes with it), `src` gives each
+// lane's criteria.
+static __device__ __forceinline__ int owner_lane(bool has) {
+  const unsigned m = __ballot_sync(0xffffffffu, has);
+  return m ? __ffs(m) - 1 : 0;
+}
+
 // a5/a6: FP32 scores of every candidate fused with the block argmax, then
-// certification.  Sets c.winner (-1 when no candidate remains).
-template <int B>
+// certification.  Sets c.winner (-1 when no candidate remains) and c.xw, the
+// winner's criteria, which travel with the reduction (each thread keeps the
+// criteria of its own leader).  In a cluster each block reduces its own
+// hosts and the blocks' leaders are combined in rank order; every branch
+// below depends only on combined values, so all blocks take it together.
+template <int B, bool CL>
 static __device__ void pick_host(const Sm& s) {
   Ctx& c = *s.c;
   const int tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
   constexpr int NW = B / 32;
   Sel me = {-1.f, INT_MAX, 0, -1.f};
-#pragma unroll 1
-  for (int u = tid; u < c.H; u += B) {
+  int32_t xb[kMaxC];
+#pragma unroll
+  for (int v = 0; v < kMaxC; ++v) xb[v] = 0;
+#pragma unroll 2
+  for (int u = c.h0 + tid; u < c.h1; u += B) {
     int32_t x[kMaxC];
     const float sc = cand_score<B>(s, u, x);
+    // hosts are visited in increasing index, so an equal score never
+    // replaces the leader
+    if (sc > me.m1) {
+#pragma unroll
+      for (int v = 0; v < kMaxC; ++v) xb[v] = x[v];
+    }
     if (sc >= 0.f) me = sel_combine(me, Sel{sc, u, 1, -1.f});
   }
+  const int mine = me.idx;
   me = sel_warp(me);
+  if (me.m1 >= 0.f && mine == me.idx) {
+#pragma unroll
+    for (int v = 0; v < kMaxC; ++v) s.xwarp[w * kMaxC + v] = xb[v];
+  }
+  __syncwarp();
   // the last warp to arrive finishes the block reduction
   Sel* ws = reinterpret_cast<Sel*>(s.sel);
   int last = 0;
@@ -847,39 +1060,93 @@ static __device__ void pick_host(const Sm& s) {
   if (last) {
     __threadfence_block();
     Sel t = lane < NW ? ws[lane] : Sel{-1.f, INT_MAX, 0, -1.f};
+    const int widx = t.idx;
     t = sel_warp(t);
+    const int ow = owner_lane(lane < NW && t.m1 >= 0.f && widx == t.idx);
+    if (lane < kMaxC) {
+      const int xv = t.m1 >= 0.f ? s.xwarp[ow * kMaxC + lane] : 0;
+      if (CL) {
+        c.xs.x[lane] = xv;
+      } else {
+        c.x1[lane] = xv;
+        c.xw[lane] = xv;
+      }
+    }
     if (lane == 0) {
-      c.m1 = t.m1;
-      c.idx1 = t.idx;
-      c.m2 = t.m2;
-      c.winner = t.m1 < 0.f ? -1 : t.idx;
-      c.arrive = t.cnt;  // hosts at the maximum (reset below)
+      c.arrive = 0;
+      if (CL) {
+        c.xs.m1 = t.m1;
+        c.xs.idx = t.idx;
+        c.xs.cnt = t.cnt;
+        c.xs.m2 = t.m2;
+      } else {
+        c.m1 = t.m1;
+        c.idx1 = t.idx;
+        c.m2 = t.m2;
+        c.cnt1 = t.cnt;
+        c.winner = t.m1 < 0.f ? -1 : t.idx;
+      }
+    }
+  }
+  if (CL) {
+    cl_sync();
+    if (w == 0) {
+      Sel t = {-1.f, INT_MAX, 0, -1.f};
+      if (lane < c.ncta) {
+        const Xch* R = cl_map(&c.xs, lane);
+        t = Sel{R->m1, R->idx, R->cnt, R->m2};
+      }
+      const int ridx = t.idx;
+      t = sel_warp(t);
+      const int orank = owner_lane(lane < c.ncta && t.m1 >= 0.f && ridx == t.idx);
+      if (lane < kMaxC) {
+        const int xv = t.m1 >= 0.f ? cl_map(&c.xs, orank)->x[lane] : 0;
+        c.x1[lane] = xv;
+        c.xw[lane] = xv;
+      }
+      if (lane == 0) {
+        c.m1 = t.m1;
+        c.idx1 = t.idx;
+        c.m2 = t.m2;
+        c.cnt1 = t.cnt;
+        c.winner = t.m1 < 0.f ? -1 : t.idx;
+      }
     }
   }
   __syncthreads();
   const float m1 = c.m1;
-  const int cnt1 = c.arrive;
+  const int cnt1 = c.cnt1;
   // guard band: every host whose FP64 score can reach the maximum has an
   // FP32 selection score >= m1 * (1 - 2^-16) (its error is below 2e-6
   // relative)
   const float thr = __fsub_rn(m1, m1 * 0x1p-16f);
   const bool band_clear = c.m2 < thr;
-  __syncthreads();
-  if (tid == 0) c.arrive = 0;
   if (m1 < 0.f || (band_clear && cnt1 == 1)) return;  // none, or a unique leader
   const int idx1 = c.idx1;
   int32_t x1[kMaxC];
-  host_crit_slow<B>(s, idx1, x1);
+#pragma unroll
+  for (int v = 0; v < kMaxC; ++v) x1[v] = c.x1[v];
   bool full = !band_clear;
   if (!full) {
     // ties at the leader's score: certified if they all carry its criteria
     bool mism = false;
 #pragma unroll 1
-    for (int u = tid; u < c.H; u += B) {
+    for (int u = c.h0 + tid; u < c.h1; u += B) {
       int32_t x[kMaxC];
       if (u != idx1 && cand_score<B>(s, u, x) == m1) mism = mism || !same_vec(x, x1, c.C);
     }
     full = __syncthreads_or(mism);
+    if (CL) {
+      if (tid == 0) c.xs.flag = full ? 1 : 0;
+      cl_sync();
+      if (w == 0) {
+        const int f = lane < c.ncta ? cl_map(&c.xs, lane)->flag : 0;
+        const bool any = __any_sync(0xffffffffu, f != 0);
+        if (lane == 0) c.full = any ? 1 : 0;
+      }
+      __syncthreads();
+      full = c.full != 0;
+    }
   }
   if (!full) return;  // c.winner = idx1
   // FP64 re-scoring of the band with the oracle's arithmetic; hosts carrying
@@ -887,26 +1154,71 @@ static __device__ void pick_host(const Sm& s) {
   // index)
   column_fp64<B>(s);
   Sel64 b = {-1.0, INT_MAX};
+#pragma unroll
+  for (int v = 0; v < kMaxC; ++v) xb[v] = 0;
 #pragma unroll 1
-  for (int u = tid; u < c.H; u += B) {
+  for (int u = c.h0 + tid; u < c.h1; u += B) {
     int32_t x[kMaxC];
-    if (cand_score<B>(s, u, x) >= thr && (u == idx1 || !same_vec(x, x1, c.C)))
-      b = sel64_combine(b, Sel64{score64(c.method, c.C, c.W, c.L1, c.norm, c.Ap, c.An, c.Td, x), u});
+    if (cand_score<B>(s, u, x) >= thr && (u == idx1 || !same_vec(x, x1, c.C))) {
+      const double sc = score64(c.method, c.C, c.W, c.L1, c.norm, c.Ap, c.An, c.Td, x);
+      if (sc > b.s) {
+#pragma unroll
+        for (int v = 0; v < kMaxC; ++v) xb[v] = x[v];
+      }
+      b = sel64_combine(b, Sel64{sc, u});
+    }
   }
+  const int mine64 = b.idx;
   for (int o = 16; o > 0; o >>= 1) {
     Sel64 q = {__shfl_xor_sync(0xffffffffu, b.s, o), __shfl_xor_sync(0xffffffffu, b.idx, o)};
     b = sel64_combine(b, q);
+  }
+  if (b.s >= 0.0 && mine64 == b.idx) {
+#pragma unroll
+    for (int v = 0; v < kMaxC; ++v) s.xwarp[w * kMaxC + v] = xb[v];
   }
   Sel64* ws64 = reinterpret_cast<Sel64*>(s.sel);
   if (lane == 0) ws64[w] = b;
   __syncthreads();
   if (w == 0) {
     Sel64 t = lane < NW ? ws64[lane] : Sel64{-1.0, INT_MAX};
+    const int widx = t.idx;
     for (int o = 16; o > 0; o >>= 1) {
       Sel64 q = {__shfl_xor_sync(0xffffffffu, t.s, o), __shfl_xor_sync(0xffffffffu, t.idx, o)};
       t = sel64_combine(t, q);
     }
-    if (lane == 0) c.winner = t.idx;
+    const int ow = owner_lane(lane < NW && t.s >= 0.0 && widx == t.idx);
+    if (lane < kMaxC) {
+      const int xv = t.s >= 0.0 ? s.xwarp[ow * kMaxC + lane] : 0;
+      if (CL) c.xs.x64[lane] = xv;
+      else c.xw[lane] = xv;
+    }
+    if (lane == 0) {
+      if (CL) {
+        c.xs.s64 = t.s;
+        c.xs.idx64 = t.idx;
+      } else {
+        c.winner = t.idx;
+      }
+    }
+  }
+  if (CL) {
+    cl_sync();
+    if (w == 0) {
+      Sel64 t = {-1.0, INT_MAX};
+      if (lane < c.ncta) {
+        const Xch* R = cl_map(&c.xs, lane);
+        t = Sel64{R->s64, R->idx64};
+      }
+      const int ridx = t.idx;
+      for (int o = 16; o > 0; o >>= 1) {
+        Sel64 q = {__shfl_xor_sync(0xffffffffu, t.s, o), __shfl_xor_sync(0xffffffffu, t.idx, o)};
+        t = sel64_combine(t, q);
+      }
+      const int orank = owner_lane(lane < c.ncta && t.s >= 0.0 && ridx == t.idx);
+      if (lane < kMaxC) c.xw[lane] = cl_map(&c.xs, orank)->x64[lane];
+      if (lane == 0) c.winner = t.idx;
+    }
   }
   __syncthreads();
 }
@@ -940,6 +1252,7 @@ static __device__ void pick_diff(const Sm& s, const InstDev& I) {
     if (lane == 0) {
       c.winner = t.s < 0.0 ? -1 : t.idx;
       c.wscore = t.s;
+      if (t.s >= 0.0) host_crit_slow<B>(s, t.idx, c.xw);
     }
   }
   __syncthreads();
@@ -968,12 +1281,16 @@ static __device__ int widest_path_warp(const Sm& s, int hs, int ht, int* links, 
   PathSel best = {-1, INT_MAX};
   const bool same_pod = ps == pt;
   const int ncand = same_pod ? half : half * half;
-  for (int i = lane; i < ncand; i += 32) {
-    const int a = same_pod ? i : div_half(c, i), cc = same_pod ? 0 : i - a * half;
+  // candidate j takes aggregation a = j mod half and core cc = j div half, so
+  // that consecutive lanes read consecutive link slots; its index for the
+  // tie-break is a * half + cc
+#pragma unroll 4
+  for (int j = lane; j < ncand; j += 32) {
+    const int cc = same_pod ? 0 : div_half(c, j), a = j - cc * half;
     int b = imin(imin(us, ut), imin(s.lk[s_ea(c, es, a)], s.lk[s_ea(c, et, a)]));
     if (!same_pod)
       b = imin(b, imin(s.lk[s_ac(c, ps * half + a, cc)], s.lk[s_ac(c, pt * half + a, cc)]));
-    best = path_combine(best, PathSel{b, i});
+    best = path_combine(best, PathSel{b, same_pod ? a : a * half + cc});
   }
   for (int o = 16; o > 0; o >>= 1) {
     PathSel q = {__shfl_xor_sync(0xffffffffu, best.b, o), __shfl_xor_sync(0xffffffffu, best.idx, o)};
@@ -991,21 +1308,107 @@ static __device__ int widest_path_warp(const Sm& s, int hs, int ht, int* links, 
   return best.b;
 }
 
-// a7/a8: commit of pod g on c.winner (warp 0).  Sets c.commit_ok; on
-// success also clears the pod's bookkeeping and sets up pod g + 1.
+// The same search by a whole block (global state: one round of memory
+// latency over all candidates instead of several per lane); every thread
+// gets the result.  The partials live in s.sel, so two calls must be
+// separated by a barrier (the reservation that follows each call ends with
+// one).
 template <int B>
-static __device__ void commit_warp(const Sm& s, const InstDev& I, int g, Pre& nxt) {
+static __device__ int widest_path_block(const Sm& s, int hs, int ht, int* links, int* nl) {
+  const Ctx& c = *s.c;
+  const int tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
+  constexpr int NW = B / 32;
+  const int half = c.half;
+  const int es = div_half(c, hs), et = div_half(c, ht), ps = div_half(c, es), pt = div_half(c, et);
+  const int us = s.lk[hs], ut = s.lk[ht];
+  if (es == et) {
+    links[0] = hs; links[1] = ht; *nl = 2;
+    return imin(us, ut);
+  }
+  PathSel best = {-1, INT_MAX};
+  const bool same_pod = ps == pt;
+  const int ncand = same_pod ? half : half * half;
+  for (int j = tid; j < ncand; j += B) {
+    const int cc = same_pod ? 0 : div_half(c, j), a = j - cc * half;
+    int b = imin(imin(us, ut), imin(s.lk[s_ea(c, es, a)], s.lk[s_ea(c, et, a)]));
+    if (!same_pod)
+      b = imin(b, imin(s.lk[s_ac(c, ps * half + a, cc)], s.lk[s_ac(c, pt * half + a, cc)]));
+    best = path_combine(best, PathSel{b, same_pod ? a : a * half + cc});
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    PathSel q = {__shfl_xor_sync(0xffffffffu, best.b, o), __shfl_xor_sync(0xffffffffu, best.idx, o)};
+    best = path_combine(best, q);
+  }
+  PathSel* ws = reinterpret_cast<PathSel*>(s.sel);
+  if (lane == 0) ws[w] = best;
+  __syncthreads();
+  best = lane < NW ? ws[lane] : PathSel{-1, INT_MAX};
+  for (int o = 16; o > 0; o >>= 1) {
+    PathSel q = {__shfl_xor_sync(0xffffffffu, best.b, o), __shfl_xor_sync(0xffffffffu, best.idx, o)};
+    best = path_combine(best, q);
+  }
+  const int a = same_pod ? best.idx : div_half(c, best.idx), cc = same_pod ? 0 : best.idx - a * half;
+  if (same_pod) {
+    links[0] = hs; links[1] = l_ea(c, es, a); links[2] = l_ea(c, et, a); links[3] = ht;
+    *nl = 4;
+  } else {
+    links[0] = hs; links[1] = l_ea(c, es, a); links[2] = l_ac(c, ps, a, cc);
+    links[3] = l_ac(c, pt, a, cc); links[4] = l_ea(c, et, a); links[5] = ht;
+    *nl = 6;
+  }
+  return best.b;
+}
+
+// Capacity part of the commit (Eqs. 4, 6), warp 0: per resource c^max for
+// every container when the host has room for the sum of maxima, else c^min.
+static __device__ void commit_capacity(const Sm& s, const InstDev& I, int g) {
   Ctx& c = *s.c;
   const int lane = lane_id();
   const int u = c.winner;
-  // decision record for the FP64 score: the criteria of u before any of
-  // this pod's reservations (rewritten by a later attempt if this one fails)
+  {
+  const uint32_t cm = s.cm[u];
+  const bool take_cpu_max = (long long)(cm & 0xffffu) >= c.dmax_cpu;
+  const bool take_mem_max = (long long)(cm >> 16) >= c.dmax_mem;
+  const int32_t c0 = c.pc[g], c1 = c.pc[g + 1];
+  uint32_t used_c = 0, used_m = 0;
+  for (int pos = c0 + lane; pos < c1; pos += 32) {
+    const int4 q = pos - c0 < 32 ? s.curc[lane] : I.c_lay[c.c_off + pos];
+    const int a = take_cpu_max ? ((unsigned)q.y >> 16) : (q.y & 0xffff);
+    const int m = take_mem_max ? ((unsigned)q.z >> 16) : (q.z & 0xffff);
+    I.o_host[c.c_off + q.x] = u;
+    I.o_cpu[c.c_off + q.x] = a;
+    I.o_mem[c.c_off + q.x] = m;
+    used_c += a;
+    used_m += m;
+  }
+  used_c = __reduce_add_sync(0xffffffffu, used_c);
+  used_m = __reduce_add_sync(0xffffffffu, used_m);
   if (lane == 0) {
+    s.cm[u] = cm - (used_c | (used_m << 16));
+    s.ctr[u] += c.size;
+  }
+  __syncwarp();
+  }
+}
+
+// a7/a8: reservations of pod g on c.winner (warp 0 of the block that writes
+// the state and the outputs).  Returns whether the pod is placed; on failure
+// nothing of this attempt stays reserved.
+// BLK: run by the whole block, the path search block-wide (global state);
+// else by warp 0.
+template <int B, bool BLK>
+static __device__ bool commit_reserve(const Sm& s, const InstDev& I, int g) {
+  Ctx& c = *s.c;
+  const int lane = lane_id();
+  const int tid = threadIdx.x;
+  const int u = c.winner;
+  // decision record for the FP64 score: the criteria of u before any of
+  // this pod's reservations, as selected (rewritten by a later attempt if
+  // this one fails)
+  if (tid == 0) {
     PodLog* L = I.scr_log + g;
-    int32_t x[kMaxC];
-    host_crit_slow<B>(s, u, x);
     for (int v = 0; v < kMaxC; ++v) {
-      L->x[v] = v < c.C ? x[v] : 0;
+      L->x[v] = v < c.C ? c.xw[v] : 0;
       L->mx[v] = c.mx[v];
       L->mn[v] = c.mn[v];
       L->S1[v] = c.S1[v];
@@ -1014,7 +1417,7 @@ static __device__ void commit_warp(const Sm& s, const InstDev& I, int g, Pre& nx
     L->n = c.n;
     L->score = c.wscore;
   }
-  __syncwarp();
+  if (BLK) __syncthreads(); else __syncwarp();
   int done = 0;  // peer links committed so far
   bool ok = true;
   for (int base = 0; base < c.npe && ok; base += 32) {
@@ -1031,30 +1434,34 @@ static __device__ void commit_warp(const Sm& s, const InstDev& I, int g, Pre& nx
       const int hs = mine_src ? u : v, ht = mine_src ? v : u;
       int32_t* path = I.o_path + (c.e_off + e) * 6;
       if (hs == ht) {
-        if (lane == 0) I.o_bw[c.e_off + e] = bmax;
+        if (tid == 0) I.o_bw[c.e_off + e] = bmax;
       } else {
         int links[6], nl = 0;
-        const int b = widest_path_warp(s, hs, ht, links, &nl);
+        const int b = BLK ? widest_path_block<B>(s, hs, ht, links, &nl)
+                          : widest_path_warp(s, hs, ht, links, &nl);
         if (b < bmin) {
           ok = false;
           break;
         }
         const int amount = b >= bmax ? bmax : bmin;
-        if (lane == 0) {
-          for (int j = 0; j < nl; ++j) {
-            s.lk[lslot(c, links[j])] -= amount;
-            path[j] = links[j];
-          }
-          I.o_bw[c.e_off + e] = amount;
+        // the links of one path are distinct: thread j reserves link j
+        int mylink = -1;
+#pragma unroll
+        for (int j = 0; j < 6; ++j)
+          if (tid == j && j < nl) mylink = links[j];
+        if (mylink >= 0) {
+          s.lk[lslot(c, mylink)] -= amount;
+          path[tid] = mylink;
         }
+        if (tid == 0) I.o_bw[c.e_off + e] = amount;
       }
       ++done;
-      __syncwarp();
+      if (BLK) __syncthreads(); else __syncwarp();
     }
   }
   if (!ok) {
     // undo this pod's reservations (links committed before the failure)
-    for (int i = lane; i < done; i += 32) {
+    for (int i = BLK ? tid : lane; i < done; i += BLK ? B : 32) {
       const int e = c.pel[i].x & kLinkIndex;
       int32_t* path = I.o_path + (c.e_off + e) * 6;
       const int bw = I.o_bw[c.e_off + e];
@@ -1065,7 +1472,24 @@ static __device__ void commit_warp(const Sm& s, const InstDev& I, int g, Pre& nx
       }
       I.o_bw[c.e_off + e] = 0;
     }
-    __syncwarp();
+    if (BLK) __syncthreads(); else __syncwarp();
+    return false;
+  }
+  if (!BLK || tid < 32) commit_capacity(s, I, g);
+  if (BLK) __syncthreads(); else __syncwarp();
+  return true;
+}
+
+// Bookkeeping of every block after the commit of pod g (warp 0): on success
+// the hosts of the pod's containers, the end of the pod and the set-up of
+// pod g + 1; on failure the winner is masked for the next pick.  Sets
+// c.commit_ok.
+template <int B>
+static __device__ void commit_finish(const Sm& s, const InstDev& I, int g, Pre& nxt, bool ok) {
+  Ctx& c = *s.c;
+  const int lane = lane_id();
+  const int u = c.winner;
+  if (!ok) {
     if (lane == 0) {
       atomicOr(&s.trymask[u % B], 1u << (u / B));
       c.nfail += 1;
@@ -1074,29 +1498,13 @@ static __device__ void commit_warp(const Sm& s, const InstDev& I, int g, Pre& nx
     __syncwarp();
     return;
   }
-  // capacity (Eqs. 4, 6): per resource c^max for every container when the
-  // host has room for the sum of maxima, else c^min
-  const uint32_t cm = s.cm[u];
-  const bool take_cpu_max = (long long)(cm & 0xffffu) >= c.dmax_cpu;
-  const bool take_mem_max = (long long)(cm >> 16) >= c.dmax_mem;
-  const int32_t c0 = c.pc[g], c1 = c.pc[g + 1];
-  uint32_t used_c = 0, used_m = 0;
-  for (int pos = c0 + lane; pos < c1; pos += 32) {
-    const int4 q = pos - c0 < 32 ? s.curc[lane] : I.c_lay[c.c_off + pos];
-    const int a = take_cpu_max ? ((unsigned)q.y >> 16) : (q.y & 0xffff);
-    const int m = take_mem_max ? ((unsigned)q.z >> 16) : (q.z & 0xffff);
-    I.o_host[c.c_off + q.x] = u;
-    I.o_cpu[c.c_off + q.x] = a;
-    I.o_mem[c.c_off + q.x] = m;
-    c.hof[q.x] = u;
-    used_c += a;
-    used_m += m;
-  }
-  used_c = __reduce_add_sync(0xffffffffu, used_c);
-  used_m = __reduce_add_sync(0xffffffffu, used_m);
-  if (lane == 0) {
-    s.cm[u] = cm - (used_c | (used_m << 16));
-    s.ctr[u] += c.size;
+  // a global hof is the output array, written by the commit itself
+  if (c.hof_smem || c.rank == 0) {
+    const int32_t c0 = c.pc[g], c1 = c.pc[g + 1];
+    for (int pos = c0 + lane; pos < c1; pos += 32) {
+      const int4 q = pos - c0 < 32 ? s.curc[lane] : I.c_lay[c.c_off + pos];
+      c.hof[q.x] = u;
+    }
   }
   __syncwarp();
   pod_clear_warp<B>(s);
@@ -1107,12 +1515,14 @@ static __device__ void commit_warp(const Sm& s, const InstDev& I, int g, Pre& nx
 }
 
 // Gives back everything the request holds (rollback of a rejected request
-// or a departure).  Block-wide; clears the outputs when `clear`.
-template <int B>
+// or a departure).  Block-wide (block 0 of a cluster, which owns the shared
+// state; then a cluster barrier); clears the outputs when `clear`.
+template <int B, bool CL>
 static __device__ void give_back(const Sm& s, const InstDev& I, int64_t c_off, int n_c,
                                  int64_t e_off, int n_e, bool clear) {
   const Ctx& c = *s.c;
   const int tid = threadIdx.x;
+  if (CL && c.rank != 0) n_c = n_e = 0;
   for (int i = tid; i < n_c; i += B) {
     const int h = I.o_host[c_off + i];
     if (h >= 0) {
@@ -1138,13 +1548,21 @@ static __device__ void give_back(const Sm& s, const InstDev& I, int64_t c_off, i
     if (clear) I.o_bw[e_off + e] = 0;
   }
   __syncthreads();
+  if (CL) cl_sync();
 }
 
-template <int B>
+template <int B, bool CL>
 static __device__ void load_instance(const Sm& s, const InstDev& I) {
   Ctx& c = *s.c;
   const int tid = threadIdx.x;
   if (tid == 0) {
+    c.rank = CL ? cl_rank() : 0;
+    c.ncta = CL ? I.ncta : 1;
+    const int ppb = I.k / c.ncta;  // pods per block
+    c.p0 = c.rank * ppb;
+    c.p1 = c.p0 + ppb;
+    c.h0 = c.p0 * I.half * I.half;
+    c.h1 = c.p1 * I.half * I.half;
     c.k = I.k; c.half = I.half; c.H = I.H; c.E = I.E; c.C = I.C; c.method = I.method;
     c.link_mbps = I.link_mbps;
     c.diff = (I.method == DC_AHP && I.rule == DC_PAIR_DIFF) ? 1 : 0;
@@ -1164,11 +1582,13 @@ static __device__ void load_instance(const Sm& s, const InstDev& I) {
     }
   }
   __syncthreads();
-  for (int u = tid; u < I.H; u += B) {
+  // a cluster shares one global copy of the state, written by block 0
+  const int hs = (CL && c.rank != 0) ? 0 : I.H;
+  for (int u = tid; u < hs; u += B) {
     s.cm[u] = (uint32_t)I.cpu[u] | ((uint32_t)I.mem[u] << 16);
     s.ctr[u] = I.ctr[u] | (I.pre[u] ? kPreBit : 0);
   }
-  for (int l = tid; l < 3 * I.H; l += B) s.lk[lslot(c, l)] = I.res[l];
+  for (int l = tid; l < 3 * hs; l += B) s.lk[lslot(c, l)] = I.res[l];
   for (int e = tid; e < I.E; e += B) s.Be[e] = 0;
   for (int p = tid; p < I.k; p += B) s.Cp[p] = 0;
   for (int h = tid; h < kHash; h += B) {
@@ -1179,12 +1599,14 @@ static __device__ void load_instance(const Sm& s, const InstDev& I) {
   s.tmark[tid] = 0;
   s.trymask[tid] = 0;
   __syncthreads();
+  if (CL) cl_sync();
 }
 
 template <int B>
 static __device__ void store_instance(const Sm& s, const InstDev& I) {
   const Ctx& c = *s.c;
   const int tid = threadIdx.x;
+  if (c.rank != 0) return;
   for (int u = tid; u < I.H; u += B) {
     const uint32_t cm = s.cm[u];
     I.cpu[u] = (int32_t)(cm & 0xffffu);
@@ -1209,7 +1631,9 @@ static __device__ void load_request(const Sm& s, const InstDev& I, int r, const 
     c.pc = stage_p ? s.st_pc : I.p_coff + q.l_off;
     c.pe = stage_p ? s.st_pe : I.p_eoff + q.l_off;
     c.hof = stage_c ? s.st_hof : I.o_host + q.c_off;
-    c.pel = q.max_pe <= kPeS ? s.pel : I.scr_pe;
+    c.hof_smem = stage_c ? 1 : 0;
+    // blocks of a cluster each have their own peer-link scratch
+    c.pel = q.max_pe <= kPeS ? s.pel : I.scr_pe + (int64_t)c.rank * I.scr_links;
     c.npe = 0;
     c.nfail = 0;
     c.ndec = 0;
@@ -1225,22 +1649,38 @@ static __device__ void load_request(const Sm& s, const InstDev& I, int r, const 
 }
 
 // One pod decision (a2..a8); pod g was set up by warp 0 before.  Returns
-// true when the pod is placed (then pod g + 1 is set up).
-template <int B, int HPT>
+// true when the pod is placed (then pod g + 1 is set up).  In a cluster,
+// block 0 commits on the shared state and the others learn the result
+// after a cluster barrier.
+template <int B, int HPT, bool CL>
 static __device__ bool decide_pod(const Sm& s, const InstDev& I, int g, Pre& nxt) {
   Ctx& c = *s.c;
   const int tid = threadIdx.x;
-  if (c.npe > 0) build_tables<B>(s);  // ends with a barrier
-  column_stats<B>(s);
+  if (c.npe > 0) tables<B>(s, I);  // ends with a barrier
+  column_stats<B, CL>(s);
   if (c.diff) diff_scores<B>(s, I);
   bool placed = false;
   for (;;) {
     if (c.diff)
       pick_diff<B>(s, I);
     else
-      pick_host<B>(s);
+      pick_host<B, CL>(s);
     if (c.winner < 0) break;
-    if (tid < 32) commit_warp<B>(s, I, g, nxt);
+    if (CL) {
+      // the state of a cluster is global: block 0 commits with all its threads
+      if (c.rank == 0) {
+        const bool ok = commit_reserve<B, true>(s, I, g);
+        if (tid == 0) c.xs.ok = ok ? 1 : 0;
+      }
+      cl_sync();
+      if (tid < 32) commit_finish<B>(s, I, g, nxt, cl_map(&c.xs, 0)->ok != 0);
+    } else if (I.state_global) {
+      const bool ok = commit_reserve<B, true>(s, I, g);
+      if (tid < 32) commit_finish<B>(s, I, g, nxt, ok);
+    } else if (tid < 32) {
+      const bool ok = commit_reserve<B, false>(s, I, g);
+      commit_finish<B>(s, I, g, nxt, ok);
+    }
     __syncthreads();
     if (c.commit_ok) {
       placed = true;
@@ -1277,23 +1717,26 @@ static __device__ void pod_scores(const Sm& s, const InstDev& I, int n_placed) {
   }
 }
 
-template <int B, int HPT>
+template <int B, int HPT, bool CL>
 static __device__ void schedule_request(const Sm& s, const InstDev& I, int r) {
   Ctx& c = *s.c;
   const int tid = threadIdx.x;
   load_request<B>(s, I, r, nullptr);
   const int64_t c_off = c.c_off, e_off = c.e_off, p_off = c.p_off;
   const int n_c = c.n_c, n_e = c.n_e, n_p = c.n_p;
-  for (int i = tid; i < n_c; i += B) {
-    I.o_host[c_off + i] = -1;
-    I.o_cpu[c_off + i] = 0;
-    I.o_mem[c_off + i] = 0;
+  const bool writer = c.rank == 0;  // outputs are written by block 0
+  if (writer) {
+    for (int i = tid; i < n_c; i += B) {
+      I.o_host[c_off + i] = -1;
+      I.o_cpu[c_off + i] = 0;
+      I.o_mem[c_off + i] = 0;
+    }
+    for (int e = tid; e < n_e; e += B) {
+      I.o_bw[e_off + e] = 0;
+      for (int j = 0; j < 6; ++j) I.o_path[(e_off + e) * 6 + j] = -1;
+    }
+    for (int p = tid; p < n_p; p += B) I.o_score[p_off + p] = -1.0;
   }
-  for (int e = tid; e < n_e; e += B) {
-    I.o_bw[e_off + e] = 0;
-    for (int j = 0; j < 6; ++j) I.o_path[(e_off + e) * 6 + j] = -1;
-  }
-  for (int p = tid; p < n_p; p += B) I.o_score[p_off + p] = -1.0;
   Pre nxt = {make_int4(0, 0, 0, 0), make_int4(0, 0, 0, 0)};
   if (tid < 32 && n_p > 0) {
     nxt = prefetch_pod(c, I, 0);
@@ -1302,20 +1745,21 @@ static __device__ void schedule_request(const Sm& s, const InstDev& I, int r) {
   __syncthreads();
   int g = 0;
   for (; g < n_p; ++g)
-    if (!decide_pod<B, HPT>(s, I, g, nxt)) break;
+    if (!decide_pod<B, HPT, CL>(s, I, g, nxt)) break;
   const bool accepted = g == n_p;
   if (accepted) {
     // links inside a pod use no network link and get bw^max
-    for (int e = tid; e < n_e; e += B) {
-      const int4 q = I.e_lay[e_off + e];
-      if (q.x & kLinkIntra) I.o_bw[e_off + (q.x & kLinkIndex)] = q.w;
-    }
+    if (writer)
+      for (int e = tid; e < n_e; e += B) {
+        const int4 q = I.e_lay[e_off + e];
+        if (q.x & kLinkIntra) I.o_bw[e_off + (q.x & kLinkIndex)] = q.w;
+      }
   } else {
-    give_back<B>(s, I, c_off, n_c, e_off, n_e, true);
+    give_back<B, CL>(s, I, c_off, n_c, e_off, n_e, true);
   }
-  pod_scores<B>(s, I, g);
+  if (writer) pod_scores<B>(s, I, g);
   __syncthreads();
-  if (tid == 0) {
+  if (tid == 0 && writer) {
     I.o_status[r] = accepted ? DC_ACCEPTED : DC_REJECTED;
     I.o_ndec[r] = c.ndec;
     I.o_tdone[r] = (long long)globaltimer_ns();
@@ -1325,13 +1769,16 @@ static __device__ void schedule_request(const Sm& s, const InstDev& I, int r) {
   __syncthreads();
 }
 
-template <int B, int HPT>
+// One data center per thread block (CL = false), or per thread-block cluster
+// of I.ncta blocks (CL = true; cluster index = descriptor index).
+template <int B, int HPT, bool CL>
 __global__ void __launch_bounds__(B, 1) k_schedule(const InstDev* __restrict__ insts) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const InstDev& I = insts[blockIdx.x];
+  const InstDev& I = insts[CL ? cl_id() : (int)blockIdx.x];
   const Sm s = carve(smem, I, B);
   if (threadIdx.x == 0) atomicMin(&I.counters[2], globaltimer_ns());
-  load_instance<B>(s, I);
+  load_instance<B, CL>(s, I);
+  const bool writer = s.c->rank == 0;
   for (int op = 0; op < I.n_ops; ++op) {
     const int w = I.ops[op];
     const int r = w & (kOpRelease - 1);
@@ -1339,14 +1786,15 @@ __global__ void __launch_bounds__(B, 1) k_schedule(const InstDev* __restrict__ i
       const int st = I.o_status[r];
       if ((st & 0xff) == DC_ACCEPTED && !(st & kReleased)) {
         const ReqRec q = I.reqs[r];
-        give_back<B>(s, I, q.c_off, q.n_c, q.e_off, q.n_e, false);
-        if (threadIdx.x == 0) I.o_status[r] = st | kReleased;
+        give_back<B, CL>(s, I, q.c_off, q.n_c, q.e_off, q.n_e, false);
+        if (threadIdx.x == 0 && writer) I.o_status[r] = st | kReleased;
       }
     } else {
-      schedule_request<B, HPT>(s, I, r);
+      schedule_request<B, HPT, CL>(s, I, r);
     }
     __syncthreads();
-    if (I.progress && threadIdx.x == 0) {
+    if (CL) cl_sync();
+    if (I.progress && threadIdx.x == 0 && writer) {
       __threadfence_system();
       *reinterpret_cast<volatile int32_t*>(I.progress) = op + 1;
     }
@@ -1354,11 +1802,13 @@ __global__ void __launch_bounds__(B, 1) k_schedule(const InstDev* __restrict__ i
   store_instance<B>(s, I);
   if (I.progress) {
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && writer) {
       __threadfence_system();
       *reinterpret_cast<volatile int32_t*>(I.progress) = I.n_ops + 1;
     }
   }
+  // no block leaves while another may still read its shared memory
+  if (CL) cl_sync();
 }
 
 // What-if ranking of pod `g` of request `r` with the given host_of, no
@@ -1371,7 +1821,7 @@ __global__ void __launch_bounds__(B, 1) k_rank(const InstDev* __restrict__ inst,
   extern __shared__ __align__(16) unsigned char smem[];
   const InstDev& I = *inst;
   const Sm s = carve(smem, I, B);
-  load_instance<B>(s, I);
+  load_instance<B, false>(s, I);
   load_request<B>(s, I, r, host_of);
   if (s.c->hof != s.st_hof) {
     // request too large to stage: the global host_of is read directly
@@ -1383,8 +1833,8 @@ __global__ void __launch_bounds__(B, 1) k_rank(const InstDev* __restrict__ inst,
     pod_setup_warp<B>(s, I, g, p);
   }
   __syncthreads();
-  if (s.c->npe > 0) build_tables<B>(s);
-  column_stats<B>(s);
+  if (s.c->npe > 0) tables<B>(s, I);
+  column_stats<B, false>(s);
   column_fp64<B>(s);
   const Ctx& c = *s.c;
   for (int u = threadIdx.x; u < c.H; u += B) {

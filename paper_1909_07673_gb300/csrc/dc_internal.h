@@ -95,6 +95,9 @@ struct InstDev {
   // gstate (global scratch, L2-resident) instead of shared memory
   int32_t state_global;
   int32_t* gstate;
+  // blocks sharing this data center (a thread-block cluster when > 1; the
+  // state is then global and k is a multiple of ncta)
+  int32_t ncta;
   int4* scr_pe;       // peer links of the pod being placed
   PodLog* scr_log;    // [pods of the current request]
   // AHP DIFF scratch, [H] each (null for the other methods): viable host
@@ -119,7 +122,7 @@ DC_HD inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 // Shared-memory layout of one scheduling block (bytes), see dc_kernels.cu.
 struct SmemLayout {
   size_t ctx, cm, ctr, lk, tab, cp, tmark, trymask, hkey, hcnt, hsum, red64, red32, sel;
-  size_t st_pc, st_pe, st_hof, pel, curc, total;
+  size_t st_pc, st_pe, st_hof, pel, curc, xwarp, wide, total;
 };
 
 // Link residuals in shared memory: host links [0, H), then edge-aggregation
@@ -156,6 +159,10 @@ DC_HD inline SmemLayout smem_layout(int k, int block, size_t ctx_bytes, bool sta
   L.st_hof = o; o = align_up(o + 4 * (size_t)kStageC, 16);
   L.pel = o; o = align_up(o + 16 * (size_t)kPeS, 16);
   L.curc = o; o = align_up(o + 16 * 32, 16);
+  L.xwarp = o; o = align_up(o + 4 * nw * kMaxC, 16);
+  // wide table passes of a global-state data center: per (pod, aggregation)
+  // and per edge switch maxima
+  L.wide = o; o = align_up(o + (state_smem ? 0 : 8 * E), 16);
   L.total = o;
   return L;
 }
@@ -166,6 +173,13 @@ int max_hosts_per_thread(int block);  // 0 for an unsupported block size
 int configure_kernels(size_t smem_max);
 // one block per descriptor of d_insts[0..n)
 int launch_schedule(int block, const InstDev* d_insts, int n, size_t smem, void* stream);
+// one thread-block cluster of ncta blocks per descriptor (block 256, 512 or
+// 1024); max_active_clusters: clusters of that shape resident at once (0:
+// the shape cannot launch)
+bool cluster_block_ok(int block);
+int launch_schedule_cluster(int block, int ncta, const InstDev* d_insts, int n, size_t smem,
+                            void* stream);
+int max_active_clusters(int block, int ncta, size_t smem, int* out);
 int launch_rank(int block, const InstDev* d_inst, int32_t req, int32_t pod, const int32_t* host_of,
                 int32_t* feas, float* s32, double* s64, int32_t* crit, int32_t* nviable,
                 size_t smem, void* stream);

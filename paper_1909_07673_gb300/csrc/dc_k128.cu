@@ -5,7 +5,7 @@
 namespace dcs {
 
 cudaError_t set_smem_attr_128(size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute(k_schedule<128, 8>,
+  cudaError_t e = cudaFuncSetAttribute(k_schedule<128, 8, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_rank<128, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -13,7 +13,7 @@ cudaError_t set_smem_attr_128(size_t smem) {
 }
 
 cudaError_t launch_schedule_128(const InstDev* d_insts, int n, size_t smem, cudaStream_t st) {
-  k_schedule<128, 8><<<n, 128, smem, st>>>(d_insts);
+  k_schedule<128, 8, false><<<n, 128, smem, st>>>(d_insts);
   return cudaGetLastError();
 }
 

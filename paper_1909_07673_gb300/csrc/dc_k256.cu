@@ -5,7 +5,7 @@
 namespace dcs {
 
 cudaError_t set_smem_attr_256(size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute(k_schedule<256, 8>,
+  cudaError_t e = cudaFuncSetAttribute(k_schedule<256, 8, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_rank<256, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -13,7 +13,7 @@ cudaError_t set_smem_attr_256(size_t smem) {
 }
 
 cudaError_t launch_schedule_256(const InstDev* d_insts, int n, size_t smem, cudaStream_t st) {
-  k_schedule<256, 8><<<n, 256, smem, st>>>(d_insts);
+  k_schedule<256, 8, false><<<n, 256, smem, st>>>(d_insts);
   return cudaGetLastError();
 }
 

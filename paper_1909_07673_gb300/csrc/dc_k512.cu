@@ -5,7 +5,7 @@
 namespace dcs {
 
 cudaError_t set_smem_attr_512(size_t smem) {
-  cudaError_t e = cudaFuncSetAttribute(k_schedule<512, 16>,
+  cudaError_t e = cudaFuncSetAttribute(k_schedule<512, 16, false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   return cudaFuncSetAttribute(k_rank<512, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -13,7 +13,7 @@ cudaError_t set_smem_attr_512(size_t smem) {
 }
 
 cudaError_t launch_schedule_512(const InstDev* d_insts, int n, size_t smem, cudaStream_t st) {
-  k_schedule<512, 16><<<n, 512, smem, st>>>(d_insts);
+  k_schedule<512, 16, false><<<n, 512, smem, st>>>(d_insts);
   return cudaGetLastError();
 }
 

@@ -64,6 +64,15 @@ DC_DECL(256)
 DC_DECL(512)
 DC_DECL(1024)
 #undef DC_DECL
+#define DC_DECL_CL(B)                                                                      \
+  cudaError_t set_cluster_attr_##B(size_t smem);                                           \
+  cudaError_t launch_schedule_cluster_##B(const InstDev* d_insts, int n, int ncta,          \
+                                          size_t smem, cudaStream_t st);                    \
+  cudaError_t max_clusters_##B(int ncta, size_t smem, int* out);
+DC_DECL_CL(256)
+DC_DECL_CL(512)
+DC_DECL_CL(1024)
+#undef DC_DECL_CL
 
 size_t ctx_bytes() { return sizeof(Ctx); }
 
@@ -72,7 +81,42 @@ int configure_kernels(size_t smem_max) {
   if (e == cudaSuccess) e = set_smem_attr_256(smem_max);
   if (e == cudaSuccess) e = set_smem_attr_512(smem_max);
   if (e == cudaSuccess) e = set_smem_attr_1024(smem_max);
+  if (e == cudaSuccess) e = set_cluster_attr_256(smem_max);
+  if (e == cudaSuccess) e = set_cluster_attr_512(smem_max);
+  if (e == cudaSuccess) e = set_cluster_attr_1024(smem_max);
   return e == cudaSuccess ? DC_OK : DC_E_CUDA;
+}
+
+bool cluster_block_ok(int block) { return block == 256 || block == 512 || block == 1024; }
+
+int launch_schedule_cluster(int block, int ncta, const InstDev* d_insts, int n, size_t smem,
+                            void* stream) {
+  if (n <= 0) return DC_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e;
+  switch (block) {
+    case 256: e = launch_schedule_cluster_256(d_insts, n, ncta, smem, st); break;
+    case 512: e = launch_schedule_cluster_512(d_insts, n, ncta, smem, st); break;
+    case 1024: e = launch_schedule_cluster_1024(d_insts, n, ncta, smem, st); break;
+    default: return DC_E_INVAL;
+  }
+  return e == cudaSuccess ? DC_OK : DC_E_CUDA;
+}
+
+int max_active_clusters(int block, int ncta, size_t smem, int* out) {
+  *out = 0;
+  cudaError_t e;
+  switch (block) {
+    case 256: e = max_clusters_256(ncta, smem, out); break;
+    case 512: e = max_clusters_512(ncta, smem, out); break;
+    case 1024: e = max_clusters_1024(ncta, smem, out); break;
+    default: return DC_E_INVAL;
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();  // an unsupported shape is not a sticky error
+    *out = 0;
+  }
+  return DC_OK;
 }
 
 int max_hosts_per_thread(int block) {

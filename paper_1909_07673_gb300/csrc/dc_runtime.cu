@@ -4,16 +4,21 @@
 // dc_submit_request), mirrors them to device arenas when a launch is
 // prepared, and keeps its data-center state resident in device memory.  A
 // launch (dc_plan) groups the instances by fat-tree size, gives each group
-// one kernel with one thread block per instance (block size from the tuning
-// table), and runs the groups concurrently on forked streams; it can be
-// captured once in a CUDA graph and replayed.
+// one kernel with one thread block, or one thread-block cluster, per
+// instance (shape from the launch table that dc_set_launch and the
+// autotuner fill), and runs the groups concurrently on forked streams; it
+// can be captured once in a CUDA graph and replayed.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "../../include/dcsched.h"
@@ -201,7 +206,7 @@ struct dc_plan {
   std::vector<uint64_t> gens;
   int flags = 0;
   struct Group {
-    int block;
+    int block, ncta;
     size_t smem;
     int first, n;
   };
@@ -225,6 +230,91 @@ struct dc_plan {
 };
 
 namespace {
+
+// Shape of one data center's scheduling launch: threads per block, blocks
+// per data center (a thread-block cluster when > 1), dynamic shared memory,
+// and whether the state lives in global scratch.
+struct LaunchCfg {
+  int block = 0, ncta = 1;
+  size_t smem = 0;
+  bool state_global = false;
+};
+
+constexpr int kMaxCluster = 16;
+
+// Process-wide launch table: (k, criteria, method, pair rule) -> (block,
+// blocks per data center).  Read when a plan is created.
+std::mutex g_launch_mu;
+std::map<std::tuple<int, int, int, int>, std::pair<int, int>> g_launch;
+
+std::tuple<int, int, int, int> launch_key(int k, int C, int method, int rule) {
+  return std::make_tuple(k, C, method, method == DC_AHP ? rule : 0);
+}
+
+// Validates a shape for data center d and fills its shared-memory size.
+int launch_shape(const dc_t* d, int block, int ncta, LaunchCfg* out) {
+  if (max_hosts_per_thread(block) == 0 || ncta < 1 || ncta > kMaxCluster) return DC_E_INVAL;
+  // one 32-bit mask word per thread tracks the hosts of a pod's neighbours
+  if (d->H > 32 * block) return DC_E_INVAL;
+  const bool diff = d->cfg.method == DC_AHP && d->cfg.pair_rule == DC_PAIR_DIFF;
+  if (ncta > 1 && (diff || !cluster_block_ok(block) || d->k % ncta != 0)) return DC_E_INVAL;
+  LaunchCfg L;
+  L.block = block;
+  L.ncta = ncta;
+  L.state_global = true;
+  if (ncta == 1 && d->k <= kMaxKSmem) {
+    const size_t sm = smem_layout(d->k, block, ctx_bytes(), true).total;
+    if (sm <= g_smem_max) {
+      L.state_global = false;
+      L.smem = sm;
+    }
+  }
+  if (L.state_global) L.smem = smem_layout(d->k, block, ctx_bytes(), false).total;
+  if (L.smem > g_smem_max) return DC_E_INVAL;
+  if (ncta > 1) {
+    int nc = 0;
+    DC_TRY(max_active_clusters(block, ncta, L.smem, &nc));
+    if (nc <= 0) return DC_E_INVAL;
+  }
+  *out = L;
+  return DC_OK;
+}
+
+// The shape a plan uses for d: the launch table's entry when it has one
+// that fits d, else the block chosen at dc_create, one block per data center.
+LaunchCfg resolve_launch(const dc_t* d) {
+  LaunchCfg L;
+  L.block = d->block;
+  L.smem = d->smem;
+  L.state_global = d->state_global;
+  std::pair<int, int> e(0, 0);
+  {
+    std::lock_guard<std::mutex> lk(g_launch_mu);
+    auto it = g_launch.find(launch_key(d->k, d->cfg.n_criteria, d->cfg.method, d->cfg.pair_rule));
+    if (it == g_launch.end()) return L;
+    e = it->second;
+  }
+  LaunchCfg T;
+  if (launch_shape(d, e.first, e.second, &T) == DC_OK) return T;
+  return L;
+}
+
+// Global state scratch and per-block peer-link scratch for shape L.
+int ensure_launch_scratch(dc_t* d, const LaunchCfg& L) {
+  if (L.state_global && !d->d_gstate) {
+    if (cudaMalloc((void**)&d->d_gstate, sizeof(int32_t) * (2 * (size_t)d->H + link_slots(d->k))) !=
+        cudaSuccess)
+      return DC_E_NOMEM;
+  }
+  if (L.ncta > 1) {
+    const size_t need = (size_t)L.ncta * std::max<size_t>(1, d->max_links);
+    if (d->d_scr_pe.cap < need) {
+      DC_TRY(d->d_scr_pe.ensure(need, 0, d->stream));
+      d->scr_links = (int32_t)d->d_scr_pe.cap;
+    }
+  }
+  return DC_OK;
+}
 
 int validate_config(const dc_config* c) {
   if (!c) return DC_E_INVAL;
@@ -396,7 +486,8 @@ int stage(dc_t* d) {
   return DC_OK;
 }
 
-InstDev make_desc(dc_t* d, const int32_t* d_ops, int n_ops, unsigned long long* counters) {
+InstDev make_desc(dc_t* d, const int32_t* d_ops, int n_ops, unsigned long long* counters,
+                  const LaunchCfg* L = nullptr) {
   InstDev I{};
   I.k = d->k; I.half = d->half; I.H = d->H; I.E = d->E;
   I.C = d->cfg.n_criteria; I.method = d->cfg.method; I.rule = d->cfg.pair_rule;
@@ -432,6 +523,13 @@ InstDev make_desc(dc_t* d, const int32_t* d_ops, int n_ops, unsigned long long* 
   I.recip = d->d_recip;
   I.state_global = d->state_global ? 1 : 0;
   I.gstate = d->d_gstate;
+  I.ncta = 1;
+  if (L) {
+    I.state_global = L->state_global ? 1 : 0;
+    I.ncta = L->ncta;
+    // each block of a cluster has its own slice of the peer-link scratch
+    I.scr_links = (int32_t)(d->d_scr_pe.cap / (size_t)L->ncta);
+  }
   I.progress = d->progress_slot;
   I.err = d->d_err;
   I.counters = counters;
@@ -448,15 +546,16 @@ int enqueue_plan(dc_plan* p, cudaStream_t st) {
   DC_CUDA(cudaMemsetAsync(p->d_counters, 0, 2 * sizeof(unsigned long long), st));
   DC_CUDA(cudaMemsetAsync(p->d_counters + 2, 0xff, sizeof(unsigned long long), st));
   const size_t G = p->groups.size();
-  if (G == 1) {
-    const auto& g = p->groups[0];
-    return launch_schedule(g.block, p->d_desc + g.first, g.n, g.smem, st);
-  }
+  auto launch = [&](const dc_plan::Group& g, cudaStream_t s) {
+    if (g.ncta > 1)
+      return launch_schedule_cluster(g.block, g.ncta, p->d_desc + g.first, g.n, g.smem, s);
+    return launch_schedule(g.block, p->d_desc + g.first, g.n, g.smem, s);
+  };
+  if (G == 1) return launch(p->groups[0], st);
   for (size_t i = 0; i < G; ++i) {
     DC_CUDA(cudaEventRecord(p->fork_ev[i], st));
     DC_CUDA(cudaStreamWaitEvent(p->side[i], p->fork_ev[i], 0));
-    const auto& g = p->groups[i];
-    DC_TRY(launch_schedule(g.block, p->d_desc + g.first, g.n, g.smem, p->side[i]));
+    DC_TRY(launch(p->groups[i], p->side[i]));
     DC_CUDA(cudaEventRecord(p->join_ev[i], p->side[i]));
   }
   for (size_t i = 0; i < G; ++i) DC_CUDA(cudaStreamWaitEvent(st, p->join_ev[i], 0));
@@ -676,7 +775,21 @@ int dc_release(dc_t* d, int64_t req_id) {
   return DC_OK;
 }
 
-int dc_plan_create(dc_t* const* dcs, int32_t n, int32_t flags, dc_plan** out) {
+}  // extern "C"
+
+namespace {
+
+// Options of plan_create beyond the public flags: at most max_ops operations
+// per instance, explicit launch shapes (one per instance) instead of the
+// launch table, and whether the plan claims its operations (trial plans of
+// the autotuner do not).
+struct PlanOpts {
+  size_t max_ops = SIZE_MAX;
+  const LaunchCfg* shapes = nullptr;
+  bool claim = true;
+};
+
+int plan_create(dc_t* const* dcs, int32_t n, int32_t flags, const PlanOpts& opt, dc_plan** out) {
   if (!dcs || n <= 0 || !out) return DC_E_INVAL;
   *out = nullptr;
   for (int32_t i = 0; i < n; ++i) {
@@ -698,11 +811,18 @@ int dc_plan_create(dc_t* const* dcs, int32_t n, int32_t flags, dc_plan** out) {
     if (rc != DC_OK) break;
     op0[i] = (flags & DC_PLAN_RESET) ? 0 : d->ops_claimed;
     op1[i] = d->ops.size();
+    if (op1[i] - op0[i] > opt.max_ops) op1[i] = op0[i] + opt.max_ops;
     all_ops.insert(all_ops.end(), d->ops.begin() + op0[i], d->ops.begin() + op1[i]);
+  }
+  std::vector<LaunchCfg> shape(n);
+  for (int32_t i = 0; i < n && rc == DC_OK; ++i) {
+    shape[i] = opt.shapes ? opt.shapes[i] : resolve_launch(dcs[i]);
+    rc = ensure_launch_scratch(dcs[i], shape[i]);
   }
   if (rc == DC_OK) {
     p->dcs.assign(dcs, dcs + n);
-    // launch order: groups of equal k, largest first; inside a group by work
+    // launch order: groups of equal k and launch shape, largest k first;
+    // inside a group by work
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i) order[i] = i;
     std::vector<double> work(n, 0.0);
@@ -715,6 +835,9 @@ int dc_plan_create(dc_t* const* dcs, int32_t n, int32_t flags, dc_plan** out) {
     }
     std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
       if (dcs[a]->k != dcs[b]->k) return dcs[a]->k > dcs[b]->k;
+      if (shape[a].block != shape[b].block) return shape[a].block > shape[b].block;
+      if (shape[a].ncta != shape[b].ncta) return shape[a].ncta > shape[b].ncta;
+      if (shape[a].smem != shape[b].smem) return shape[a].smem > shape[b].smem;
       return work[a] > work[b];
     });
     std::vector<size_t> op_base(n);
@@ -735,10 +858,18 @@ int dc_plan_create(dc_t* const* dcs, int32_t n, int32_t flags, dc_plan** out) {
     for (int j = 0; j < n && rc == DC_OK; ++j) {
       const int i = order[j];
       dc_t* d = dcs[i];
-      p->h_desc.push_back(make_desc(d, p->d_ops + op_base[i], (int)(op1[i] - op0[i]), p->d_counters));
+      const LaunchCfg& L = shape[i];
+      p->h_desc.push_back(
+          make_desc(d, p->d_ops + op_base[i], (int)(op1[i] - op0[i]), p->d_counters, &L));
+      if (!opt.claim) p->h_desc.back().progress = nullptr;
       p->inst_of.push_back(i);
-      if (p->groups.empty() || dcs[order[p->groups.back().first]]->k != d->k)
-        p->groups.push_back({d->block, d->smem, j, 0});
+      bool same = !p->groups.empty();
+      if (same) {
+        const auto& g = p->groups.back();
+        same = dcs[order[g.first]]->k == d->k && g.block == L.block && g.ncta == L.ncta &&
+               g.smem == L.smem;
+      }
+      if (!same) p->groups.push_back({L.block, L.ncta, L.smem, j, 0});
       p->groups.back().n += 1;
     }
     if (rc == DC_OK)
@@ -797,11 +928,178 @@ int dc_plan_create(dc_t* const* dcs, int32_t n, int32_t flags, dc_plan** out) {
     p->req_begin.push_back(rb);
     p->req_end.push_back(re);
     p->n_ops.push_back((int32_t)(op1[i] - op0[i]));
-    d->ops_claimed = op1[i];
+    if (opt.claim) d->ops_claimed = op1[i];
     p->gens.push_back(d->gen);
   }
   *out = p;
   return DC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dc_plan_create(dc_t* const* dcs, int32_t n, int32_t flags, dc_plan** out) {
+  return plan_create(dcs, n, flags, PlanOpts{}, out);
+}
+
+}  // extern "C"
+
+namespace {
+
+// Device time of one state-resetting launch of the first max_ops operations
+// of every instance with shapes sh (best of two launches after a warm-up).
+int time_plan(dc_t* const* dcs, int32_t n, size_t max_ops, const std::vector<LaunchCfg>& sh,
+              cudaEvent_t e0, cudaEvent_t e1, double* ms) {
+  dc_plan* p = nullptr;
+  PlanOpts o;
+  o.max_ops = max_ops;
+  o.shapes = sh.data();
+  o.claim = false;
+  DC_TRY(plan_create(dcs, n, DC_PLAN_RESET, o, &p));
+  cudaStream_t st = p->home;
+  int rc = DC_OK;
+  double best = 1e300;
+  for (int r = 0; r < 3 && rc == DC_OK; ++r) {
+    rc = cuda_rc(cudaEventRecord(e0, st));
+    if (rc == DC_OK) rc = dc_plan_launch(p, st);
+    if (rc == DC_OK) rc = cuda_rc(cudaEventRecord(e1, st));
+    if (rc == DC_OK) rc = cuda_rc(cudaEventSynchronize(e1));
+    float t = 0.f;
+    if (rc == DC_OK) rc = cuda_rc(cudaEventElapsedTime(&t, e0, e1));
+    if (r > 0) best = std::min(best, (double)t);
+  }
+  dc_plan_destroy(p);
+  *ms = best;
+  return rc;
+}
+
+bool same_shape(const LaunchCfg& a, const LaunchCfg& b) {
+  return a.block == b.block && a.ncta == b.ncta;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dc_autotune(dc_t* const* dcs, int32_t n, int32_t max_ops, dc_tune_entry* out,
+                int32_t max_out, int32_t* n_out) {
+  if (!dcs || n <= 0 || max_ops < 0 || (max_out > 0 && !out)) return DC_E_INVAL;
+  for (int32_t i = 0; i < n; ++i) {
+    if (!dcs[i]) return DC_E_INVAL;
+    for (int32_t j = 0; j < i; ++j)
+      if (dcs[j] == dcs[i]) return DC_E_INVAL;
+  }
+  DC_TRY(ensure_configured());
+  const size_t lim = max_ops > 0 ? (size_t)max_ops : SIZE_MAX;
+  // kinds of data center, by decreasing work (pods x hosts of the ops run)
+  struct Kind {
+    std::tuple<int, int, int, int> key;
+    std::vector<int> members;
+    double work = 0;
+    std::vector<LaunchCfg> cands;
+  };
+  std::vector<Kind> kinds;
+  std::vector<LaunchCfg> cur(n);
+  for (int32_t i = 0; i < n; ++i) {
+    dc_t* d = dcs[i];
+    settle(d, true);
+    DC_CUDA(cudaStreamSynchronize(d->stream));
+    const auto key = launch_key(d->k, d->cfg.n_criteria, d->cfg.method, d->cfg.pair_rule);
+    size_t q = 0;
+    while (q < kinds.size() && kinds[q].key != key) ++q;
+    if (q == kinds.size()) {
+      kinds.push_back(Kind());
+      kinds.back().key = key;
+    }
+    kinds[q].members.push_back(i);
+    double c = 0;
+    for (size_t o = 0; o < d->ops.size() && o < lim; ++o)
+      if (!(d->ops[o] & kOpRelease)) c += d->reqs.p[d->ops[o]].n_p;
+    kinds[q].work += c * d->H;
+    cur[i] = resolve_launch(d);
+  }
+  std::stable_sort(kinds.begin(), kinds.end(),
+                   [](const Kind& a, const Kind& b) { return a.work > b.work; });
+  const int blocks[] = {128, 256, 512, 1024};
+  const int nctas[] = {1, 2, 3, 4, 6, 8, 12, 16};
+  for (Kind& kd : kinds) {
+    const dc_t* rep = dcs[kd.members[0]];
+    for (int b : blocks)
+      for (int c : nctas) {
+        // a cluster only pays with a few hundred hosts per block
+        if (c > 1 && rep->H / c < 256) continue;
+        LaunchCfg L;
+        if (launch_shape(rep, b, c, &L) == DC_OK) kd.cands.push_back(L);
+      }
+  }
+  // the trials overwrite the device state: keep a copy
+  std::vector<int32_t*> saved(n, nullptr);
+  int rc = DC_OK;
+  for (int32_t i = 0; i < n && rc == DC_OK; ++i) {
+    const size_t bytes = sizeof(int32_t) * 7 * (size_t)dcs[i]->H;
+    if (cudaMalloc((void**)&saved[i], bytes) != cudaSuccess) rc = DC_E_NOMEM;
+    else rc = cuda_rc(cudaMemcpy(saved[i], dcs[i]->d_state, bytes, cudaMemcpyDeviceToDevice));
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (rc == DC_OK) rc = cuda_rc(cudaEventCreate(&e0));
+  if (rc == DC_OK) rc = cuda_rc(cudaEventCreate(&e1));
+  double best = 0;
+  if (rc == DC_OK) rc = time_plan(dcs, n, lim, cur, e0, e1, &best);
+  int32_t written = 0;
+  for (size_t q = 0; q < kinds.size() && rc == DC_OK; ++q) {
+    Kind& kd = kinds[q];
+    if (kd.work <= 0) continue;
+    const LaunchCfg before = cur[kd.members[0]];
+    const double ms0 = best;
+    LaunchCfg chosen = before;
+    int trials = 0;
+    for (const LaunchCfg& L : kd.cands) {
+      if (same_shape(L, before)) continue;
+      std::vector<LaunchCfg> sh = cur;
+      for (int i : kd.members) sh[i] = L;
+      double t = 0;
+      rc = time_plan(dcs, n, lim, sh, e0, e1, &t);
+      if (rc != DC_OK) break;
+      ++trials;
+      if (t < 0.97 * best) {
+        best = t;
+        chosen = L;
+      }
+    }
+    if (rc != DC_OK) break;
+    for (int i : kd.members) cur[i] = chosen;
+    {
+      std::lock_guard<std::mutex> lk(g_launch_mu);
+      g_launch[kd.key] = std::make_pair(chosen.block, chosen.ncta);
+    }
+    if (written < max_out) {
+      dc_tune_entry& e = out[written++];
+      e.k = std::get<0>(kd.key);
+      e.n_criteria = std::get<1>(kd.key);
+      e.method = std::get<2>(kd.key);
+      e.pair_rule = std::get<3>(kd.key);
+      e.block = chosen.block;
+      e.ncta = chosen.ncta;
+      e.block0 = before.block;
+      e.ncta0 = before.ncta;
+      e.trials = trials;
+      e.ms = best;
+      e.ms0 = ms0;
+    }
+  }
+  for (int32_t i = 0; i < n; ++i)
+    if (saved[i]) {
+      const size_t bytes = sizeof(int32_t) * 7 * (size_t)dcs[i]->H;
+      if (cudaMemcpy(dcs[i]->d_state, saved[i], bytes, cudaMemcpyDeviceToDevice) != cudaSuccess &&
+          rc == DC_OK)
+        rc = DC_E_CUDA;
+      cudaFree(saved[i]);
+    }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (n_out) *n_out = (int32_t)kinds.size();
+  return rc;
 }
 
 int dc_plan_launch(dc_plan* p, void* cuda_stream) {
@@ -944,6 +1242,43 @@ int dc_query_state(dc_t* d, int32_t field, int32_t* out, int64_t len) {
   if (len < n) return DC_E_INVAL;
   DC_CUDA(cudaStreamSynchronize(d->stream));
   DC_CUDA(cudaMemcpy(out, d->d_state + off, n * 4, cudaMemcpyDeviceToHost));
+  return DC_OK;
+}
+
+int dc_set_launch(int32_t k, int32_t n_criteria, int32_t method, int32_t pair_rule,
+                  int32_t block, int32_t ncta) {
+  if (k < 2 || k > kMaxK || (k & 1) || (n_criteria != 4 && n_criteria != 6) ||
+      (method != DC_TOPSIS && method != DC_AHP) ||
+      (pair_rule != DC_PAIR_RATIO && pair_rule != DC_PAIR_DIFF))
+    return DC_E_INVAL;
+  const auto key = launch_key(k, n_criteria, method, pair_rule);
+  if (block == 0) {
+    std::lock_guard<std::mutex> lk(g_launch_mu);
+    g_launch.erase(key);
+    return DC_OK;
+  }
+  DC_TRY(ensure_configured());
+  dc_t t;
+  t.k = k;
+  t.half = k / 2;
+  t.H = k * k * k / 4;
+  t.E = k * k / 2;
+  t.cfg.n_criteria = n_criteria;
+  t.cfg.method = method;
+  t.cfg.pair_rule = pair_rule;
+  LaunchCfg L;
+  DC_TRY(launch_shape(&t, block, ncta, &L));
+  std::lock_guard<std::mutex> lk(g_launch_mu);
+  g_launch[key] = std::make_pair((int)block, (int)ncta);
+  return DC_OK;
+}
+
+int dc_get_launch(const dc_t* d, int32_t* block, int32_t* ncta, int64_t* smem_bytes) {
+  if (!d) return DC_E_INVAL;
+  const LaunchCfg L = resolve_launch(d);
+  if (block) *block = L.block;
+  if (ncta) *ncta = L.ncta;
+  if (smem_bytes) *smem_bytes = (int64_t)L.smem;
   return DC_OK;
 }
 

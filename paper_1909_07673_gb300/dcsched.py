@@ -60,6 +60,13 @@ class _ServerStats(C.Structure):
                 ("wall_s", C.c_double)]
 
 
+class _TuneEntry(C.Structure):
+    _fields_ = [("k", C.c_int32), ("n_criteria", C.c_int32), ("method", C.c_int32),
+                ("pair_rule", C.c_int32), ("block", C.c_int32), ("ncta", C.c_int32),
+                ("block0", C.c_int32), ("ncta0", C.c_int32), ("trials", C.c_int32),
+                ("pad", C.c_int32), ("ms", C.c_double), ("ms0", C.c_double)]
+
+
 _lib = None
 
 
@@ -102,6 +109,10 @@ def lib():
         L.dc_plan_stats.argtypes = [C.c_void_p, _i64p, _i64p, _i32p, _i64p]
         L.dc_plan_destroy.argtypes = [C.c_void_p]
         L.dc_plan_destroy.restype = None
+        L.dc_set_launch.argtypes = [C.c_int32] * 6
+        L.dc_get_launch.argtypes = [C.c_void_p, _i32p, _i32p, _i64p]
+        L.dc_autotune.argtypes = [C.POINTER(C.c_void_p), C.c_int32, C.c_int32,
+                                  C.POINTER(_TuneEntry), C.c_int32, _i32p]
         _lib = L
     return _lib
 
@@ -336,6 +347,35 @@ class Server:
 
     def __del__(self):
         self.close()
+
+
+def set_launch(k: int, n_criteria: int, method: int, pair_rule: int, block: int,
+               ncta: int = 1) -> None:
+    """Records the scheduling-kernel shape (threads per block, blocks per
+    data center) for data centers of this kind (dc_set_launch); block 0
+    removes the entry."""
+    _check(lib().dc_set_launch(k, n_criteria, method, pair_rule, block, ncta), "dc_set_launch")
+
+
+def autotune(dcs: Sequence["DataCenter"], max_ops: int = 0) -> List[Dict[str, float]]:
+    """Chooses the launch shape of every kind of data center among dcs for
+    the batched launch of their queued operations (dc_autotune; only the
+    first max_ops operations of each, 0 = all) and records it.  Returns one
+    dict per kind."""
+    out = (_TuneEntry * 64)()
+    n = C.c_int32()
+    _check(lib().dc_autotune(_handles(list(dcs)), len(dcs), max_ops, out, 64, C.byref(n)),
+           "dc_autotune")
+    return [{f: getattr(out[i], f) for f, _ in _TuneEntry._fields_ if f != "pad"}
+            for i in range(min(n.value, 64))]
+
+
+def get_launch(dc: "DataCenter"):
+    """(block, blocks per data center, dynamic shared memory bytes) a plan
+    would use for dc."""
+    b, n, sm = C.c_int32(), C.c_int32(), C.c_int64()
+    _check(lib().dc_get_launch(dc.h, C.byref(b), C.byref(n), C.byref(sm)), "dc_get_launch")
+    return b.value, n.value, sm.value
 
 
 def load_instance(inst, stream=None, max_requests: Optional[int] = None) -> DataCenter:
