@@ -65,6 +65,8 @@ def parse():
                     help="operations per data center run in each autotuner trial")
     ap.add_argument("--no-largest", action="store_true",
                     help="skip the single k=48 data-center measurement")
+    ap.add_argument("--largest-requests", type=int, default=200,
+                    help="requests of the k=48 data center")
     return ap.parse_args()
 
 
@@ -325,7 +327,7 @@ def run_largest(args, ds, torch, peak):
 
     inst = W.k48().instances[0]
     stream = torch.cuda.Stream()
-    dc = ds.load_instance(inst, stream=stream)
+    dc = ds.load_instance(inst, stream=stream, max_requests=args.largest_requests)
     tuned = None if args.no_autotune else ds.autotune([dc], max_ops=8)
     plan = ds.Plan([dc], ds.PLAN_RESET)
     times = []
@@ -342,13 +344,13 @@ def run_largest(args, ds, torch, peak):
     dec, hr, nk, _ = plan.stats()
     ms = statistics.mean(times)
     block, ncta, _ = ds.get_launch(dc)
-    acc = sum(dc.status(r)[0] == ds.ACCEPTED for r in range(inst.reqs.n))
+    acc = sum(dc.status(r)[0] == ds.ACCEPTED for r in range(min(inst.reqs.n, args.largest_requests)))
     gbs = hr * BYTES_PER_HOST_RANKING / (ms * 1e-3) / 1e9
     plan.close()
     dc.close()
     return {
-        "workload": "one k=48 fat-tree (27,648 hosts), 200 requests of 64-512 containers in "
-                    "pods of 1-8, TOPSIS, 6 criteria",
+        "workload": "one k=48 fat-tree (27,648 hosts), %d requests of 64-512 containers in "
+                    "pods of 1-8, TOPSIS, 6 criteria" % min(inst.reqs.n, args.largest_requests),
         "host_rankings_per_s": hr / (ms * 1e-3), "decisions_per_s": dec / (ms * 1e-3),
         "us_per_decision": ms * 1e3 / dec, "ms_per_launch": ms, "decisions": dec,
         "accepted_requests": int(acc),

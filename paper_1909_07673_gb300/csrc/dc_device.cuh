@@ -67,7 +67,7 @@ struct Xch {
   long long S1[kMaxC], S2[kMaxC];  // column statistics over the block's hosts
   int32_t mx[kMaxC], mn[kMaxC];
   int32_t n;
-  int32_t flag;                    // tie certification: a tie with other criteria
+  int32_t flag;                    // Lead::mixed of the block
   float m1, m2;                    // block argmax (see Sel)
   int32_t idx, cnt;
   int32_t x[kMaxC];                // criteria of the block's leader
@@ -120,13 +120,14 @@ struct Ctx {
   int32_t nvc;      // viable hosts counted by the AHP DIFF compaction
   double wscore;    // AHP DIFF: exact global priority of the winner
   int32_t cnt1;     // hosts at the maximum FP32 score
-  int32_t full;     // certification needs the FP64 band
+  int32_t mixed;    // some host at the maximum has other criteria than idx1
   int32_t x1[kMaxC];  // criteria of the leader idx1
   int32_t xw[kMaxC];  // criteria of the winner (its decision record)
   // blocks sharing the data center (a thread-block cluster; 1 block: rank 0
   // of 1): this block ranks the hosts [h0, h1) of pods [p0, p1) and builds
   // their switch tables; block 0 alone writes the shared state and outputs
   int32_t rank, ncta, p0, p1, h0, h1;
+  int32_t gstate;    // the state lives in global memory
   int32_t hof_smem;  // hof is this block's shared copy
   Xch xs;
 };
@@ -148,7 +149,7 @@ struct Sm {
   int32_t *st_pc, *st_pe, *st_hof;
   int4* pel;
   int4* curc;  // [32] container records of the pod being placed
-  int32_t* xwarp;  // [B / 32][kMaxC] criteria of each warp's leader
+  int32_t* xwarp;  // [B / 32][kMaxC + 1] criteria of each warp's leader, mixed flag
   int32_t *wg, *wm;  // [E] each: wide table passes (global-state data centers)
 };
 
@@ -620,13 +621,10 @@ static __device__ void build_tables(const Sm& s) {
       const int ev = div_half(c, v), pv = div_half(c, ev);
       int gm = -1;
       if (active && p != pv) {
-        // independent loads: unrolled so that several are in flight
-#pragma unroll 8
         for (int cc = 0; cc < half; ++cc)
           gm = imax(gm, imin(s.lk[s_ac(c, p * half + a, cc)], s.lk[s_ac(c, pv * half + a, cc)]));
       }
       int mid = -1;
-#pragma unroll 8
       for (int a2 = 0; a2 < half; ++a2) {
         const int g2 = __shfl_sync(0xffffffffu, gm, gbase + a2);
         if (active) {
@@ -742,8 +740,7 @@ static __device__ void column_stats(const Sm& s) {
   int mx[kMaxC], mn[kMaxC];
 #pragma unroll
   for (int v = 0; v < kMaxC; ++v) { s1[v] = 0; s2[v] = 0; mx[v] = INT_MIN; mn[v] = INT_MAX; }
-#pragma unroll 2
-  for (int u = c.h0 + tid; u < c.h1; u += B) {
+  auto visit = [&](int u) {
     int32_t x[kMaxC];
     if (host_crit<B>(s, u, x)) {
       ++cnt;
@@ -757,6 +754,14 @@ static __device__ void column_stats(const Sm& s) {
         }
       }
     }
+  };
+  // a global state: two hosts in flight hide part of the L2 latency
+  if (CL || c.gstate) {
+#pragma unroll 2
+    for (int u = c.h0 + tid; u < c.h1; u += B) visit(u);
+  } else {
+#pragma unroll 1
+    for (int u = c.h0 + tid; u < c.h1; u += B) visit(u);
   }
   // warp level: 32-bit redux (sum of squares split in 24-bit halves)
   const uint32_t wc = __reduce_add_sync(0xffffffffu, cnt);
@@ -997,6 +1002,42 @@ static __device__ __forceinline__ Sel64 sel64_combine(Sel64 a, Sel64 b) {
   return {a.s, imin(a.idx, b.idx)};
 }
 
+// Selection state of a set of hosts: the maximum FP32 score m1 (-1: none),
+// its lowest host index, the number of hosts at it, the largest score below
+// it, whether some host at the maximum carries criteria other than the
+// leader's (then their FP64 scores may differ), and the leader's criteria.
+struct Lead {
+  float m1, m2;
+  int idx, cnt;
+  bool mixed;
+  int32_t x[kMaxC];
+};
+
+// Combines the Lead of every lane of a warp; all lanes get the result.
+// Scores are >= 0 or -1, so their bit patterns order like the floats and the
+// warp's integer reductions apply.
+static __device__ __forceinline__ Lead lead_warp(const Lead& me, int C) {
+  const unsigned full = 0xffffffffu;
+  const int mb = __float_as_int(me.m1);
+  const int Mb = __reduce_max_sync(full, mb);
+  const bool at = mb == Mb && me.m1 >= 0.f;
+  Lead r;
+  r.m1 = __int_as_float(Mb);
+  r.idx = __reduce_min_sync(full, at ? me.idx : INT_MAX);
+  r.cnt = (int)__reduce_add_sync(full, at ? (uint32_t)me.cnt : 0u);
+  r.m2 = __int_as_float(__reduce_max_sync(full, __float_as_int(at ? me.m2 : me.m1)));
+  const unsigned lm = __ballot_sync(full, at && me.idx == r.idx);
+  const int lead = lm ? __ffs(lm) - 1 : 0;
+#pragma unroll
+  for (int v = 0; v < kMaxC; ++v) r.x[v] = __shfl_sync(full, me.x[v], lead);
+  r.mixed = __any_sync(full, at && (me.mixed || !same_vec(me.x, r.x, C)));
+  return r;
+}
+
+// Lead records of warps / blocks in shared memory: Sel part in s.sel, the
+// criteria and the mixed flag in s.xwarp ([kMaxC + 1] per record).
+constexpr int kXw = kMaxC + 1;
+
 // FP32 selection score of host u, or -1 when u is not viable, its commit
 // must fail, or it failed a commit already.
 template <int B>
@@ -1016,55 +1057,86 @@ static __device__ __forceinline__ int owner_lane(bool has) {
 
 // a5/a6: FP32 scores of every candidate fused with the block argmax, then
 // certification.  Sets c.winner (-1 when no candidate remains) and c.xw, the
-// winner's criteria, which travel with the reduction (each thread keeps the
-// criteria of its own leader).  In a cluster each block reduces its own
-// hosts and the blocks' leaders are combined in rank order; every branch
+// winner's criteria.  One pass: every thread keeps the Lead of its hosts
+// (leader criteria included), warps and blocks combine Leads, so ties at the
+// maximum are certified without another pass (they are, when every host at
+// the maximum carries the leader's criteria).  In a cluster each block
+// reduces its own hosts and the blocks' Leads are combined; every branch
 // below depends only on combined values, so all blocks take it together.
 template <int B, bool CL>
 static __device__ void pick_host(const Sm& s) {
   Ctx& c = *s.c;
   const int tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
   constexpr int NW = B / 32;
-  Sel me = {-1.f, INT_MAX, 0, -1.f};
-  int32_t xb[kMaxC];
+  const int C = c.C;
+  Lead me;
+  me.m1 = -1.f;
+  me.m2 = -1.f;
+  me.idx = INT_MAX;
+  me.cnt = 0;
+  me.mixed = false;
 #pragma unroll
-  for (int v = 0; v < kMaxC; ++v) xb[v] = 0;
-#pragma unroll 2
-  for (int u = c.h0 + tid; u < c.h1; u += B) {
+  for (int v = 0; v < kMaxC; ++v) me.x[v] = 0;
+  auto visit = [&](int u) {
     int32_t x[kMaxC];
     const float sc = cand_score<B>(s, u, x);
-    // hosts are visited in increasing index, so an equal score never
-    // replaces the leader
+    // hosts are visited in increasing index: an equal score keeps the leader
     if (sc > me.m1) {
+      me.m2 = me.m1;
+      me.m1 = sc;
+      me.idx = u;
+      me.cnt = 1;
+      me.mixed = false;
 #pragma unroll
-      for (int v = 0; v < kMaxC; ++v) xb[v] = x[v];
+      for (int v = 0; v < kMaxC; ++v) me.x[v] = x[v];
+    } else if (sc == me.m1) {
+      if (sc >= 0.f) {
+        me.cnt += 1;
+        me.mixed = me.mixed || !same_vec(x, me.x, C);
+      }
+    } else {
+      me.m2 = fmaxf(me.m2, sc);
     }
-    if (sc >= 0.f) me = sel_combine(me, Sel{sc, u, 1, -1.f});
+  };
+  if (CL || c.gstate) {
+#pragma unroll 2
+    for (int u = c.h0 + tid; u < c.h1; u += B) visit(u);
+  } else {
+#pragma unroll 1
+    for (int u = c.h0 + tid; u < c.h1; u += B) visit(u);
   }
-  const int mine = me.idx;
-  me = sel_warp(me);
-  if (me.m1 >= 0.f && mine == me.idx) {
-#pragma unroll
-    for (int v = 0; v < kMaxC; ++v) s.xwarp[w * kMaxC + v] = xb[v];
-  }
-  __syncwarp();
-  // the last warp to arrive finishes the block reduction
+  Lead wl = lead_warp(me, C);
   Sel* ws = reinterpret_cast<Sel*>(s.sel);
+  if (lane == 0) {
+    ws[w] = Sel{wl.m1, wl.idx, wl.cnt, wl.m2};
+#pragma unroll
+    for (int v = 0; v < kMaxC; ++v) s.xwarp[w * kXw + v] = wl.x[v];
+    s.xwarp[w * kXw + kMaxC] = wl.mixed ? 1 : 0;
+  }
+  // the last warp to arrive finishes the block reduction
   int last = 0;
   if (lane == 0) {
-    ws[w] = me;
     __threadfence_block();
     last = atomicAdd(&c.arrive, 1) == NW - 1;
   }
   last = __shfl_sync(0xffffffffu, last, 0);
   if (last) {
     __threadfence_block();
-    Sel t = lane < NW ? ws[lane] : Sel{-1.f, INT_MAX, 0, -1.f};
-    const int widx = t.idx;
-    t = sel_warp(t);
-    const int ow = owner_lane(lane < NW && t.m1 >= 0.f && widx == t.idx);
+    Lead t;
+    const Sel q = lane < NW ? ws[lane] : Sel{-1.f, INT_MAX, 0, -1.f};
+    t.m1 = q.m1;
+    t.idx = q.idx;
+    t.cnt = q.cnt;
+    t.m2 = q.m2;
+#pragma unroll
+    for (int v = 0; v < kMaxC; ++v) t.x[v] = lane < NW ? s.xwarp[lane * kXw + v] : 0;
+    t.mixed = lane < NW && s.xwarp[lane * kXw + kMaxC] != 0;
+    t = lead_warp(t, C);
     if (lane < kMaxC) {
-      const int xv = t.m1 >= 0.f ? s.xwarp[ow * kMaxC + lane] : 0;
+      int xv = 0;
+#pragma unroll
+      for (int v = 0; v < kMaxC; ++v)
+        if (v == lane) xv = t.x[v];
       if (CL) {
         c.xs.x[lane] = xv;
       } else {
@@ -1079,11 +1151,13 @@ static __device__ void pick_host(const Sm& s) {
         c.xs.idx = t.idx;
         c.xs.cnt = t.cnt;
         c.xs.m2 = t.m2;
+        c.xs.flag = t.mixed ? 1 : 0;
       } else {
         c.m1 = t.m1;
         c.idx1 = t.idx;
         c.m2 = t.m2;
         c.cnt1 = t.cnt;
+        c.mixed = t.mixed ? 1 : 0;
         c.winner = t.m1 < 0.f ? -1 : t.idx;
       }
     }
@@ -1091,16 +1165,30 @@ static __device__ void pick_host(const Sm& s) {
   if (CL) {
     cl_sync();
     if (w == 0) {
-      Sel t = {-1.f, INT_MAX, 0, -1.f};
+      Lead t;
+      t.m1 = -1.f;
+      t.m2 = -1.f;
+      t.idx = INT_MAX;
+      t.cnt = 0;
+      t.mixed = false;
+#pragma unroll
+      for (int v = 0; v < kMaxC; ++v) t.x[v] = 0;
       if (lane < c.ncta) {
         const Xch* R = cl_map(&c.xs, lane);
-        t = Sel{R->m1, R->idx, R->cnt, R->m2};
+        t.m1 = R->m1;
+        t.idx = R->idx;
+        t.cnt = R->cnt;
+        t.m2 = R->m2;
+        t.mixed = R->flag != 0;
+#pragma unroll
+        for (int v = 0; v < kMaxC; ++v) t.x[v] = R->x[v];
       }
-      const int ridx = t.idx;
-      t = sel_warp(t);
-      const int orank = owner_lane(lane < c.ncta && t.m1 >= 0.f && ridx == t.idx);
+      t = lead_warp(t, C);
       if (lane < kMaxC) {
-        const int xv = t.m1 >= 0.f ? cl_map(&c.xs, orank)->x[lane] : 0;
+        int xv = 0;
+#pragma unroll
+        for (int v = 0; v < kMaxC; ++v)
+          if (v == lane) xv = t.x[v];
         c.x1[lane] = xv;
         c.xw[lane] = xv;
       }
@@ -1109,46 +1197,26 @@ static __device__ void pick_host(const Sm& s) {
         c.idx1 = t.idx;
         c.m2 = t.m2;
         c.cnt1 = t.cnt;
+        c.mixed = t.mixed ? 1 : 0;
         c.winner = t.m1 < 0.f ? -1 : t.idx;
       }
     }
   }
   __syncthreads();
   const float m1 = c.m1;
-  const int cnt1 = c.cnt1;
   // guard band: every host whose FP64 score can reach the maximum has an
   // FP32 selection score >= m1 * (1 - 2^-16) (its error is below 2e-6
-  // relative)
+  // relative).  Certified without FP64: nothing else in the band, and every
+  // host at the maximum carries the leader's criteria (same FP64 score, the
+  // lowest index wins).
   const float thr = __fsub_rn(m1, m1 * 0x1p-16f);
   const bool band_clear = c.m2 < thr;
-  if (m1 < 0.f || (band_clear && cnt1 == 1)) return;  // none, or a unique leader
+  if (m1 < 0.f || (band_clear && (c.cnt1 == 1 || !c.mixed))) return;
   const int idx1 = c.idx1;
   int32_t x1[kMaxC];
 #pragma unroll
   for (int v = 0; v < kMaxC; ++v) x1[v] = c.x1[v];
-  bool full = !band_clear;
-  if (!full) {
-    // ties at the leader's score: certified if they all carry its criteria
-    bool mism = false;
-#pragma unroll 1
-    for (int u = c.h0 + tid; u < c.h1; u += B) {
-      int32_t x[kMaxC];
-      if (u != idx1 && cand_score<B>(s, u, x) == m1) mism = mism || !same_vec(x, x1, c.C);
-    }
-    full = __syncthreads_or(mism);
-    if (CL) {
-      if (tid == 0) c.xs.flag = full ? 1 : 0;
-      cl_sync();
-      if (w == 0) {
-        const int f = lane < c.ncta ? cl_map(&c.xs, lane)->flag : 0;
-        const bool any = __any_sync(0xffffffffu, f != 0);
-        if (lane == 0) c.full = any ? 1 : 0;
-      }
-      __syncthreads();
-      full = c.full != 0;
-    }
-  }
-  if (!full) return;  // c.winner = idx1
+  int32_t xb[kMaxC];
   // FP64 re-scoring of the band with the oracle's arithmetic; hosts carrying
   // the leader's vector are represented by the leader (same score, lower
   // index)
@@ -1175,7 +1243,7 @@ static __device__ void pick_host(const Sm& s) {
   }
   if (b.s >= 0.0 && mine64 == b.idx) {
 #pragma unroll
-    for (int v = 0; v < kMaxC; ++v) s.xwarp[w * kMaxC + v] = xb[v];
+    for (int v = 0; v < kMaxC; ++v) s.xwarp[w * kXw + v] = xb[v];
   }
   Sel64* ws64 = reinterpret_cast<Sel64*>(s.sel);
   if (lane == 0) ws64[w] = b;
@@ -1189,7 +1257,7 @@ static __device__ void pick_host(const Sm& s) {
     }
     const int ow = owner_lane(lane < NW && t.s >= 0.0 && widx == t.idx);
     if (lane < kMaxC) {
-      const int xv = t.s >= 0.0 ? s.xwarp[ow * kMaxC + lane] : 0;
+      const int xv = t.s >= 0.0 ? s.xwarp[ow * kXw + lane] : 0;
       if (CL) c.xs.x64[lane] = xv;
       else c.xw[lane] = xv;
     }
@@ -1284,7 +1352,6 @@ static __device__ int widest_path_warp(const Sm& s, int hs, int ht, int* links, 
   // candidate j takes aggregation a = j mod half and core cc = j div half, so
   // that consecutive lanes read consecutive link slots; its index for the
   // tie-break is a * half + cc
-#pragma unroll 4
   for (int j = lane; j < ncand; j += 32) {
     const int cc = same_pod ? 0 : div_half(c, j), a = j - cc * half;
     int b = imin(imin(us, ut), imin(s.lk[s_ea(c, es, a)], s.lk[s_ea(c, et, a)]));
@@ -1563,6 +1630,7 @@ static __device__ void load_instance(const Sm& s, const InstDev& I) {
     c.p1 = c.p0 + ppb;
     c.h0 = c.p0 * I.half * I.half;
     c.h1 = c.p1 * I.half * I.half;
+    c.gstate = I.state_global;
     c.k = I.k; c.half = I.half; c.H = I.H; c.E = I.E; c.C = I.C; c.method = I.method;
     c.link_mbps = I.link_mbps;
     c.diff = (I.method == DC_AHP && I.rule == DC_PAIR_DIFF) ? 1 : 0;

@@ -159,7 +159,7 @@ DC_HD inline SmemLayout smem_layout(int k, int block, size_t ctx_bytes, bool sta
   L.st_hof = o; o = align_up(o + 4 * (size_t)kStageC, 16);
   L.pel = o; o = align_up(o + 16 * (size_t)kPeS, 16);
   L.curc = o; o = align_up(o + 16 * 32, 16);
-  L.xwarp = o; o = align_up(o + 4 * nw * kMaxC, 16);
+  L.xwarp = o; o = align_up(o + 4 * nw * (kMaxC + 1), 16);
   // wide table passes of a global-state data center: per (pod, aggregation)
   // and per edge switch maxima
   L.wide = o; o = align_up(o + (state_smem ? 0 : 8 * E), 16);
