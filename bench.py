@@ -67,6 +67,13 @@ def parse():
                     help="skip the single k=48 data-center measurement")
     ap.add_argument("--largest-requests", type=int, default=200,
                     help="requests of the k=48 data center")
+    ap.add_argument("--largest-shape", default="",
+                    help="fixed launch shape BLOCKxBLOCKS_PER_DC for the k=48 data center "
+                         "(default: autotuned)")
+    ap.add_argument("--largest-only", action="store_true",
+                    help="only the k=48 data-center measurement (one JSON line)")
+    ap.add_argument("--no-comparators", action="store_true",
+                    help="skip the method comparison (TOPSIS, AHP, best fit, worst fit)")
     return ap.parse_args()
 
 
@@ -316,6 +323,51 @@ def run_serving(args, ds, torch):
     }
 
 
+# ----------------------------------------------------------------- method comparison
+
+def run_comparators(args, ds, torch):
+    """The k=16 workload (1,024 hosts, 0-70 % pre-load, 1,000 requests of
+    4-64 containers) with [min, max] intervals, scheduled by TOPSIS, AHP and
+    the best-fit / worst-fit comparators: device time, acceptance, mean
+    utilities (Eqs. 1-2) and the final fragmentation."""
+    from paper_1909_07673_gb300 import workloads as W
+
+    out = {}
+    stream = torch.cuda.Stream()
+    for name, method in (("TOPSIS", W.TOPSIS), ("AHP", W.AHP), ("BF", W.BF), ("WF", W.WF)):
+        inst = W.k16(method=method, intervals=True).instances[0]
+        dc = ds.load_instance(inst, stream=stream)
+        plan = ds.Plan([dc], ds.PLAN_RESET)
+        times = []
+        for rep in range(3):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plan.launch(stream)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if rep > 0:
+                times.append(e0.elapsed_time(e1))
+        plan.collect()
+        dec, hr, _, _ = plan.stats()
+        ms = statistics.mean(times)
+        acc = sum(dc.status(r)[0] == ds.ACCEPTED for r in range(inst.reqs.n))
+        u = dc.utility_summary()
+        act_s, act_l, f_s, f_l = dc.fragmentation()
+        out[name] = {
+            "ms_per_launch": ms, "decisions": dec, "host_rankings_per_s": hr / (ms * 1e-3),
+            "accepted_requests": int(acc),
+            "mean_u_container": u["sum_u_container"] / max(1, u["n_containers"]),
+            "mean_u_link": u["sum_u_link"] / max(1, u["n_links"]),
+            "f_servers": f_s, "f_links": f_l,
+        }
+        plan.close()
+        dc.close()
+    return {"workload": "one k=16 fat-tree (1,024 hosts, 0-70 % pre-load), 1,000 requests of "
+                        "4-64 containers with [min, max] intervals, 6 criteria",
+            "methods": out}
+
+
 # ----------------------------------------------------------------- largest fat-tree
 
 def run_largest(args, ds, torch, peak):
@@ -328,7 +380,12 @@ def run_largest(args, ds, torch, peak):
     inst = W.k48().instances[0]
     stream = torch.cuda.Stream()
     dc = ds.load_instance(inst, stream=stream, max_requests=args.largest_requests)
-    tuned = None if args.no_autotune else ds.autotune([dc], max_ops=8)
+    tuned = None
+    if args.largest_shape:
+        b, n = (int(x) for x in args.largest_shape.lower().split("x"))
+        ds.set_launch(inst.k, inst.n_criteria, inst.method, inst.pair_rule, b, n)
+    elif not args.no_autotune:
+        tuned = ds.autotune([dc], max_ops=8)
     plan = ds.Plan([dc], ds.PLAN_RESET)
     times = []
     for rep in range(3):
@@ -365,6 +422,20 @@ def run_largest(args, ds, torch, peak):
 
 # ----------------------------------------------------------------- ours
 
+def run_largest_only(args):
+    import torch
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1909_07673_gb300 import dcsched as ds
+
+    peak, _ = measured_peak()
+    print(json.dumps({"largest_fat_tree": run_largest(args, ds, torch, peak)}), flush=True)
+    return 0
+
+
 def run_ours(args):
     import torch
 
@@ -381,6 +452,10 @@ def run_ours(args):
     __graft_entry__.build()
     from paper_1909_07673_gb300 import dcsched as ds
 
+    # the serving replay first, on an otherwise idle device (rank 0)
+    serving = None if (args.no_serving or rank != 0) else run_serving(args, ds, torch)
+    if dist:
+        dist.barrier()
     wl = workload(args, rank)
     stream = torch.cuda.Stream()
     dcs = [ds.load_instance(inst, stream=stream) for inst in wl.instances]
@@ -475,11 +550,11 @@ def run_ours(args):
     achieved = hr * BYTES_PER_HOST_RANKING / (ms_kernel * 1e-3) / 1e9
     traffic = ncu_traffic(hr)
     largest = None if args.no_largest else run_largest(args, ds, torch, peak)
+    comparators = None if (args.no_comparators or rank != 0) else run_comparators(args, ds, torch)
     if rank != 0:
         if dist:
             dist.barrier()
         return 0
-    serving = None if args.no_serving else run_serving(args, ds, torch)
     cpu_hr, cpu_s, cpu_desc, _, cpu_threads = oracle_sample(wl, args.cpu_seconds,
                                                             os.cpu_count() or 1)
     one_hr, one_s, one_desc, _, _ = oracle_sample(wl, max(2.0, args.cpu_seconds / 3), 1)
@@ -525,6 +600,8 @@ def run_ours(args):
         line["serving"] = serving
     if largest is not None:
         line["largest_fat_tree"] = largest
+    if comparators is not None:
+        line["comparators"] = comparators
     print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
@@ -535,6 +612,8 @@ def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.largest_only:
+        return run_largest_only(args)
     return run_ours(args)
 
 

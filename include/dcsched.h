@@ -58,8 +58,16 @@ enum {
   DC_E_BUSY = -6      /* state does not allow the call (e.g. stale plan) */
 };
 
-/* ranking method (Sec. V) */
-enum { DC_TOPSIS = 0, DC_AHP = 1 };
+/* ranking method: the multi-criteria methods of Sec. V, and the best-fit /
+ * worst-fit comparators of the evaluation (Sec. IV-A: the orchestrators'
+ * binpacking and spread, which ignore the network; the path search follows
+ * the choice of host).  Best / worst fit: a host is viable when its free CPU
+ * and memory cover the pod's minimum; it is ranked by K = free_cpu *
+ * host_mem + free_mem * host_cpu (smallest first for best fit, largest for
+ * worst fit, lowest index on ties); the commit is the one of the other
+ * methods; the pod score is the chosen host's (free_cpu / host_cpu +
+ * free_mem / host_mem) / 2 before placement. */
+enum { DC_TOPSIS = 0, DC_AHP = 1, DC_BF = 2, DC_WF = 3 };
 /* AHP pairwise rule: RATIO a_ij = (x_i+1)/(x_j+1) (consistent, default);
  * DIFF the difference rule of Sec. V-B made reciprocal:
  * a_ij = d, 1/|d| or 1 for d = x_i - x_j > 0, < 0, = 0. */
@@ -215,6 +223,31 @@ int dc_plan_stats(dc_plan* plan, int64_t* decisions, int64_t* host_rankings,
  * by this instance since dc_create. */
 int dc_io_stats(dc_t* dc, int64_t* h2d_bytes, int64_t* d2h_bytes);
 void dc_plan_destroy(dc_plan* plan);
+
+/* --- utilities and fragmentation (Sec. II-B, Eqs. 1-2) --------------------
+ * Computed on the device from the instance's results and state, FP64 with
+ * every operation rounded in the order written.
+ *
+ * dc_utilities: for request req_id, u_container[i] = (cpu_i / cpu_max_i +
+ * mem_i / mem_max_i) / 2 (Eq. 1 over the resources CPU and memory) and
+ * u_link[e] = bw_e / bw_max_e (Eq. 2 read as the bandwidth the link's path
+ * carries over its maximum; a link inside one host has bw_max); a maximum of
+ * 0 counts 1; every entry of a request that was not accepted is 0.  Arrays
+ * [n_containers] / [n_edges], caller-allocated.  DC_E_BUSY while the request
+ * has not been scheduled by a completed launch (waits for launches in
+ * flight).
+ * dc_utility_summary: sums of U(i) and U(ij) over the accepted requests among
+ * those scheduled so far (each request's terms in index order, then the
+ * requests in order) and the numbers of containers and links summed.
+ * dc_fragmentation: active servers (hosting a container or pre-loaded) and
+ * active links (residual below capacity) of the current state, F(N^s) =
+ * active servers / servers and F(E^s) = active links / links; waits for
+ * launches in flight.  Any output pointer may be NULL. */
+int dc_utilities(dc_t* dc, int64_t req_id, double* u_container, double* u_link);
+int dc_utility_summary(dc_t* dc, double* sum_u_container, int64_t* n_containers,
+                       double* sum_u_link, int64_t* n_links);
+int dc_fragmentation(dc_t* dc, int64_t* active_servers, int64_t* active_links,
+                     double* f_servers, double* f_links);
 
 /* --- launch shapes --------------------------------------------------------
  * No counterpart in the paper (a GPU launch parameter).  The scheduling

@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
 
-TOPSIS, AHP = 0, 1
+TOPSIS, AHP, BF, WF = 0, 1, 2, 3
 RATIO, DIFF = 0, 1
 ACCEPTED, REJECTED = 1, 2
 FREE_CPU, FREE_MEM, CTR, PRE, LINK_RES = 0, 1, 2, 3, 4
@@ -82,6 +82,10 @@ def lib():
         L.orc_ahp_weights.argtypes = [C.c_int32, _f64p, C.c_int32, _f64p]
         L.orc_ahp.argtypes = [C.c_int32, C.c_int32, _i64p, _f64p, C.c_int32, _f64p]
         L.orc_ahp_literal.argtypes = [C.c_int32, C.c_int32, _i64p, _f64p, C.c_int32, _f64p]
+        L.orc_utilities.argtypes = [C.POINTER(_Request), C.POINTER(_Result), _f64p, _f64p]
+        L.orc_utilities.restype = None
+        L.orc_fragmentation.argtypes = [C.c_void_p, _i64p, _i64p, _f64p, _f64p]
+        L.orc_fragmentation.restype = None
     return _lib
 
 
@@ -182,6 +186,13 @@ class OracleDC:
         if lib().orc_set_state(self.h, field, _p(a, _i32p), len(a)) != 0:
             raise ValueError("bad field")
 
+    def fragmentation(self):
+        """(active servers, active links, F(N^s), F(E^s)) of the current state."""
+        a, b = C.c_int64(), C.c_int64()
+        fs, fl = C.c_double(), C.c_double()
+        lib().orc_fragmentation(self.h, C.byref(a), C.byref(b), C.byref(fs), C.byref(fl))
+        return a.value, b.value, fs.value, fl.value
+
     def widest_path(self, u: int, v: int):
         links = np.zeros(6, np.int32)
         hops = C.c_int32()
@@ -199,6 +210,22 @@ class OracleDC:
         if F < 0:
             raise ValueError("orc_rank_pod failed: %d" % F)
         return feas.astype(bool), crit.reshape(self.H, self.n_criteria), score
+
+
+def utilities(q: Dict[str, np.ndarray], out: Dict[str, np.ndarray]):
+    """U(i) per container and U(ij) per link of a scheduled request (Eqs. 1-2);
+    `out` is what OracleDC.schedule returned."""
+    rq = _Req(q)
+    n, m = len(rq.a["pod"]), len(rq.a["src"])
+    keep = {k: np.ascontiguousarray(out[k], np.int32) for k in ("host", "cpu", "mem", "bw", "path")}
+    ps = np.ascontiguousarray(out["pod_score"], np.float64)
+    res = _Result(int(out["status"]), int(out.get("n_decisions", 0)),
+                  *(_p(keep[x], _i32p) for x in ("host", "cpu", "mem", "bw", "path")),
+                  _p(ps, _f64p))
+    uc = np.zeros(n, np.float64)
+    ue = np.zeros(m, np.float64)
+    lib().orc_utilities(C.byref(rq.s), C.byref(res), _p(uc, _f64p), _p(ue, _f64p))
+    return uc, ue
 
 
 def run_instance(inst, max_requests: Optional[int] = None) -> List[Dict[str, np.ndarray]]:

@@ -157,7 +157,7 @@ int orc_create(const orc_config* cfg, const int32_t* pre_cpu, const int32_t* pre
   if (cfg->k < 2 || (cfg->k & 1) || cfg->k > 254) return ORC_EINVAL;
   if (cfg->host_cpu < 0 || cfg->host_mem < 0 || cfg->link_mbps < 0) return ORC_EINVAL;
   if (cfg->n_criteria != 4 && cfg->n_criteria != 6) return ORC_EINVAL;
-  if (cfg->method != ORC_TOPSIS && cfg->method != ORC_AHP) return ORC_EINVAL;
+  if (cfg->method < ORC_TOPSIS || cfg->method > ORC_WF) return ORC_EINVAL;
   if (cfg->pair_rule != ORC_RATIO && cfg->pair_rule != ORC_DIFF) return ORC_EINVAL;
   double wsum = 0.0;
   for (int v = 0; v < cfg->n_criteria; ++v) {
@@ -595,11 +595,52 @@ static int host_criteria(const orc_dc* d, const pod_ctx* c, int32_t u, int64_t* 
   return feasible;
 }
 
+/* Best fit / worst fit [Sec. IV-A: the orchestrators' native binpacking and
+ * spread, which ignore the network; the shortest-path search comes after the
+ * host is chosen].  Readings: a host is viable when its free CPU and memory
+ * cover the pod's minimum demand (no network condition); hosts are ranked by
+ * their free capacity normalised per resource, K = free_cpu * host_mem +
+ * free_mem * host_cpu (an exact integer, proportional to free_cpu / host_cpu
+ * + free_mem / host_mem): worst fit takes the largest K, best fit the
+ * smallest; equal keys by increasing index; the commit (paths, retry on
+ * failure, rollback) is the multi-criteria methods' one.  The reported pod
+ * score is the chosen host's (free_cpu / host_cpu + free_mem / host_mem) / 2
+ * before placement. */
+static int is_fit(const orc_dc* d) { return d->cfg.method == ORC_BF || d->cfg.method == ORC_WF; }
+
+static double fit_share(int32_t f, int32_t cap) { return cap > 0 ? (double)f / (double)cap : 0.0; }
+
+static double fit_score(const orc_dc* d, int32_t u) {
+  return (fit_share(d->free_cpu[u], d->cfg.host_cpu) + fit_share(d->free_mem[u], d->cfg.host_mem)) /
+         2.0;
+}
+
+static int32_t rank_fit(const orc_dc* d, const pod_ctx* c, int32_t* feas, double* score) {
+  const int64_t hc = d->cfg.host_cpu, hm = d->cfg.host_mem;
+  const int64_t kmax = 2 * hc * hm;
+  int32_t F = 0;
+  for (int32_t u = 0; u < d->H; ++u) {
+    feas[u] = d->free_cpu[u] >= c->dmin_cpu && d->free_mem[u] >= c->dmin_mem;
+    score[u] = NAN;
+    if (!feas[u]) continue;
+    const int64_t K = (int64_t)d->free_cpu[u] * hm + (int64_t)d->free_mem[u] * hc;
+    score[u] = (double)(d->cfg.method == ORC_WF ? K : kmax - K);  /* exact */
+    ++F;
+  }
+  return F;
+}
+
 /* Scores every viable host; returns F, fills feas[H] and score[H] (NaN when
  * not viable) and, if crit != NULL, crit[H * C]. */
 static int32_t rank_with_ctx(const orc_dc* d, const pod_ctx* c, int32_t* feas,
                              int64_t* crit, double* score) {
   const int32_t C = d->cfg.n_criteria;
+  if (is_fit(d)) {
+    const int32_t F = rank_fit(d, c, feas, score);
+    if (crit)
+      for (int32_t u = 0; u < d->H; ++u) host_criteria(d, c, u, crit + (int64_t)u * C);
+    return F;
+  }
   int64_t* xall = (int64_t*)malloc(sizeof(int64_t) * d->H * C);
   int64_t* xf = (int64_t*)malloc(sizeof(int64_t) * d->H * C);
   int32_t* idx = (int32_t*)malloc(sizeof(int32_t) * d->H);
@@ -797,9 +838,10 @@ int orc_schedule(orc_dc* d, const orc_request* q, orc_result* r) {
       int32_t u = next_candidate(d->H, feas, score, tried);
       if (u < 0) break;
       tried[u] = 1;
+      const double fs = is_fit(d) ? fit_score(d, u) : 0.0;  /* before placement */
       if (try_commit(d, q, g, u, &c, host_of, r)) {
         placed = 1;
-        r->pod_score[g] = score[u];
+        r->pod_score[g] = is_fit(d) ? fs : score[u];
         break;
       }
     }
@@ -830,4 +872,43 @@ int orc_release(orc_dc* d, const orc_request* q, const orc_result* r) {
   if (r->status != ORC_ACCEPTED) return ORC_EINVAL;
   give_back(d, q, r);
   return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Utilities [Sec. II-B, Eqs. 1-2] and fragmentation [Sec. II-B].
+ * Readings: Eq. 1 averages allocated/maximum over the resources R = {CPU,
+ * memory}; Eq. 2 sums the bandwidth allocated over the links of the path,
+ * which the paper's own remark (optimal utility 1 at the maximum) only fits
+ * when it is read as the bandwidth the path carries for the link (the same on
+ * every link of the path) over bw_max.  A maximum of 0 is fully satisfied
+ * (utility 1).  A server is active when it hosts containers or carries
+ * pre-load (the flag f_u of the criteria), a link when some bandwidth of it is
+ * in use (residual below capacity). */
+static double util_term(int32_t a, int32_t mx) {
+  return mx > 0 ? (double)a / (double)mx : 1.0;
+}
+
+void orc_utilities(const orc_request* q, const orc_result* r, double* u_c, double* u_e) {
+  const int acc = r->status == ORC_ACCEPTED;
+  for (int32_t i = 0; i < q->n_containers; ++i) {
+    if (!acc || r->host[i] < 0) {
+      u_c[i] = 0.0;
+      continue;
+    }
+    const double sum = util_term(r->cpu[i], q->cpu_max[i]) + util_term(r->mem[i], q->mem_max[i]);
+    u_c[i] = sum / 2.0;
+  }
+  for (int32_t e = 0; e < q->n_edges; ++e)
+    u_e[e] = acc ? util_term(r->bw[e], q->bw_max[e]) : 0.0;
+}
+
+void orc_fragmentation(const orc_dc* d, int64_t* act_s, int64_t* act_l, double* f_s,
+                       double* f_l) {
+  int64_t ns = 0, nl = 0;
+  for (int64_t h = 0; h < d->H; ++h) ns += (d->ctr[h] > 0 || d->pre[h]) ? 1 : 0;
+  for (int64_t l = 0; l < d->L; ++l) nl += d->res[l] < d->cfg.link_mbps ? 1 : 0;
+  if (act_s) *act_s = ns;
+  if (act_l) *act_l = nl;
+  if (f_s) *f_s = (double)ns / (double)d->H;
+  if (f_l) *f_l = (double)nl / (double)d->L;
 }

@@ -36,7 +36,9 @@
 extern "C" {
 #endif
 
-enum { ORC_TOPSIS = 0, ORC_AHP = 1 };
+/* methods: the multi-criteria rankings, and the best-fit / worst-fit
+ * comparators of the evaluation (binpacking / spread) */
+enum { ORC_TOPSIS = 0, ORC_AHP = 1, ORC_BF = 2, ORC_WF = 3 };
 enum { ORC_RATIO = 0, ORC_DIFF = 1 };
 enum { ORC_PENDING = 0, ORC_ACCEPTED = 1, ORC_REJECTED = 2 };
 enum { ORC_OK = 0, ORC_EINVAL = -1, ORC_ENOMEM = -2 };
@@ -56,7 +58,7 @@ typedef struct {
   int32_t host_mem;   /* memory units per host */
   int32_t link_mbps;  /* bandwidth of every link */
   int32_t n_criteria; /* 4 or 6 */
-  int32_t method;     /* ORC_TOPSIS | ORC_AHP */
+  int32_t method;     /* ORC_TOPSIS | ORC_AHP | ORC_BF | ORC_WF */
   int32_t pair_rule;  /* ORC_RATIO | ORC_DIFF (AHP only) */
   double weights[6];  /* criteria weights W, >= 0 */
 } orc_config;
@@ -107,6 +109,23 @@ int32_t orc_rank_pod(const orc_dc* dc, const orc_request* req, int32_t g,
                      const int32_t* host_of, int32_t* feasible, int64_t* crit,
                      double* score);
 
+/* Utilities of a request's placement [Sec. II-B, Eqs. 1-2]:
+ *   u_container[i] = (cpu_i / cpu_max_i + mem_i / mem_max_i) / 2, the mean
+ *   over the |R| = 2 resources of allocated over maximum (a term whose maximum
+ *   is 0 counts 1);
+ *   u_link[e] = bw_e / bw_max_e, the bandwidth allocated on every link of the
+ *   link's path over its maximum (1 when the maximum is 0; a link inside one
+ *   host gets bw_max, so 1).
+ * Every entry of a rejected request is 0.  FP64, each operation rounded, in
+ * the order written. */
+void orc_utilities(const orc_request* req, const orc_result* res, double* u_container,
+                   double* u_link);
+/* Fragmentation of the current state [Sec. II-B]: F(N^s) = active servers /
+ * servers (active: hosts a container or carries pre-load), F(E^s) = active
+ * links / links (active: residual below the link capacity).  Any output may
+ * be NULL. */
+void orc_fragmentation(const orc_dc* dc, int64_t* active_servers, int64_t* active_links,
+                       double* f_servers, double* f_links);
 /* Scoring primitives over a viable-host matrix x[F * C] (row-major per host). */
 void orc_topsis(int32_t F, int32_t C, const int64_t* x, const double* W, double* cl);
 void orc_ahp_weights(int32_t C, const double* W, int32_t rule, double* L1);

@@ -127,6 +127,8 @@ struct Ctx {
   // of 1): this block ranks the hosts [h0, h1) of pods [p0, p1) and builds
   // their switch tables; block 0 alone writes the shared state and outputs
   int32_t rank, ncta, p0, p1, h0, h1;
+  int32_t fit, wf;     // best fit / worst fit (fit = 1; wf = 1 for worst fit)
+  int32_t hcpu, hmem;  // host capacities
   int32_t gstate;    // the state lives in global memory
   int32_t hof_smem;  // hof is this block's shared copy
   Xch xs;
@@ -1291,6 +1293,90 @@ static __device__ void pick_host(const Sm& s) {
   __syncthreads();
 }
 
+// Best fit / worst fit (the orchestrators' binpacking / spread, which ignore
+// the network): a host is viable when its free CPU and memory cover the
+// pod's minimum; the key K = free_cpu * host_mem + free_mem * host_cpu (exact
+// integer, the free capacity normalised per resource) is maximised (worst
+// fit) or minimised (best fit), lowest index on ties, among the hosts whose
+// commit can succeed and that did not fail one.  Keys are exact doubles, so
+// the argmax needs no certification.  Sets c.winner and c.xw = {free CPU,
+// free memory} of the winner (its decision record).
+template <int B, bool CL>
+static __device__ void pick_fit(const Sm& s) {
+  Ctx& c = *s.c;
+  const int tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
+  constexpr int NW = B / 32;
+  const long long hc = c.hcpu, hm = c.hmem, kmax = 2 * hc * hm;
+  Sel64 b = {-1.0, INT_MAX};
+  int xc = 0, xm = 0;
+  for (int u = c.h0 + tid; u < c.h1; u += B) {
+    if ((s.trymask[u % B] >> (u / B)) & 1u) continue;
+    const uint32_t cm = s.cm[u];
+    const int cpu = (int)(cm & 0xffffu), mem = (int)(cm >> 16);
+    if (cpu < c.dmin_cpu || mem < c.dmin_mem || !commit_possible<B>(s, u)) continue;
+    const long long K = (long long)cpu * hm + (long long)mem * hc;
+    const double key = (double)(c.wf ? K : kmax - K);
+    if (key > b.s) {
+      xc = cpu;
+      xm = mem;
+    }
+    b = sel64_combine(b, Sel64{key, u});
+  }
+  const int mine = b.idx;
+  for (int o = 16; o > 0; o >>= 1) {
+    Sel64 q = {__shfl_xor_sync(0xffffffffu, b.s, o), __shfl_xor_sync(0xffffffffu, b.idx, o)};
+    b = sel64_combine(b, q);
+  }
+  if (b.s >= 0.0 && mine == b.idx) {
+    s.xwarp[w * kXw + 0] = xc;
+    s.xwarp[w * kXw + 1] = xm;
+  }
+  Sel64* ws64 = reinterpret_cast<Sel64*>(s.sel);
+  if (lane == 0) ws64[w] = b;
+  __syncthreads();
+  if (w == 0) {
+    Sel64 t = lane < NW ? ws64[lane] : Sel64{-1.0, INT_MAX};
+    const int widx = t.idx;
+    for (int o = 16; o > 0; o >>= 1) {
+      Sel64 q = {__shfl_xor_sync(0xffffffffu, t.s, o), __shfl_xor_sync(0xffffffffu, t.idx, o)};
+      t = sel64_combine(t, q);
+    }
+    const int ow = owner_lane(lane < NW && t.s >= 0.0 && widx == t.idx);
+    if (lane < kMaxC) {
+      const int xv = (t.s >= 0.0 && lane < 2) ? s.xwarp[ow * kXw + lane] : 0;
+      if (CL) c.xs.x64[lane] = xv;
+      else c.xw[lane] = xv;
+    }
+    if (lane == 0) {
+      if (CL) {
+        c.xs.s64 = t.s;
+        c.xs.idx64 = t.idx;
+      } else {
+        c.winner = t.s < 0.0 ? -1 : t.idx;
+      }
+    }
+  }
+  if (CL) {
+    cl_sync();
+    if (w == 0) {
+      Sel64 t = {-1.0, INT_MAX};
+      if (lane < c.ncta) {
+        const Xch* R = cl_map(&c.xs, lane);
+        t = Sel64{R->s64, R->idx64};
+      }
+      const int ridx = t.idx;
+      for (int o = 16; o > 0; o >>= 1) {
+        Sel64 q = {__shfl_xor_sync(0xffffffffu, t.s, o), __shfl_xor_sync(0xffffffffu, t.idx, o)};
+        t = sel64_combine(t, q);
+      }
+      const int orank = owner_lane(lane < c.ncta && t.s >= 0.0 && ridx == t.idx);
+      if (lane < kMaxC) c.xw[lane] = t.s >= 0.0 ? cl_map(&c.xs, orank)->x64[lane] : 0;
+      if (lane == 0) c.winner = t.s < 0.0 ? -1 : t.idx;
+    }
+  }
+  __syncthreads();
+}
+
 // a6 under AHP DIFF: exact FP64 argmax (lowest index on ties) over the viable
 // hosts whose commit can succeed and that did not fail one.
 template <int B>
@@ -1631,6 +1717,10 @@ static __device__ void load_instance(const Sm& s, const InstDev& I) {
     c.h0 = c.p0 * I.half * I.half;
     c.h1 = c.p1 * I.half * I.half;
     c.gstate = I.state_global;
+    c.fit = (I.method == DC_BF || I.method == DC_WF) ? 1 : 0;
+    c.wf = I.method == DC_WF ? 1 : 0;
+    c.hcpu = I.host_cpu;
+    c.hmem = I.host_mem;
     c.k = I.k; c.half = I.half; c.H = I.H; c.E = I.E; c.C = I.C; c.method = I.method;
     c.link_mbps = I.link_mbps;
     c.diff = (I.method == DC_AHP && I.rule == DC_PAIR_DIFF) ? 1 : 0;
@@ -1724,12 +1814,16 @@ template <int B, int HPT, bool CL>
 static __device__ bool decide_pod(const Sm& s, const InstDev& I, int g, Pre& nxt) {
   Ctx& c = *s.c;
   const int tid = threadIdx.x;
-  if (c.npe > 0) tables<B>(s, I);  // ends with a barrier
-  column_stats<B, CL>(s);
-  if (c.diff) diff_scores<B>(s, I);
+  if (!c.fit) {
+    if (c.npe > 0) tables<B>(s, I);  // ends with a barrier
+    column_stats<B, CL>(s);
+    if (c.diff) diff_scores<B>(s, I);
+  }
   bool placed = false;
   for (;;) {
-    if (c.diff)
+    if (c.fit)
+      pick_fit<B, CL>(s);
+    else if (c.diff)
       pick_diff<B>(s, I);
     else
       pick_host<B, CL>(s);
@@ -1772,6 +1866,13 @@ static __device__ void pod_scores(const Sm& s, const InstDev& I, int n_placed) {
     const PodLog* L = I.scr_log + g;
     if (c.diff) {
       I.o_score[c.p_off + g] = L->score;
+      continue;
+    }
+    if (c.fit) {
+      // (free_cpu / host_cpu + free_mem / host_mem) / 2 of the chosen host
+      const double a = c.hcpu > 0 ? __ddiv_rn((double)L->x[0], (double)c.hcpu) : 0.0;
+      const double m = c.hmem > 0 ? __ddiv_rn((double)L->x[1], (double)c.hmem) : 0.0;
+      I.o_score[c.p_off + g] = __ddiv_rn(__dadd_rn(a, m), 2.0);
       continue;
     }
     double norm[kMaxC], Ap[kMaxC], An[kMaxC], Td[kMaxC];
@@ -1908,11 +2009,22 @@ __global__ void __launch_bounds__(B, 1) k_rank(const InstDev* __restrict__ inst,
   for (int u = threadIdx.x; u < c.H; u += B) {
     int32_t x[kMaxC];
     const bool f = host_crit<B>(s, u, x);
+    for (int v = 0; v < c.C; ++v) crit[(int64_t)u * c.C + v] = x[v];
+    if (c.fit) {
+      // capacity-only viability and the exact best-fit / worst-fit key
+      const bool ff = x[0] >= c.dmin_cpu && x[1] >= c.dmin_mem;
+      const long long hc = c.hcpu, hm = c.hmem;
+      const long long K = (long long)x[0] * hm + (long long)x[1] * hc;
+      const double key = (double)(c.wf ? K : 2 * hc * hm - K);
+      feas[u] = ff ? 1 : 0;
+      s32[u] = ff ? (float)key : __int_as_float(0x7fc00000);
+      s64[u] = ff ? key : __longlong_as_double(0x7ff8000000000000ll);
+      continue;
+    }
     feas[u] = f ? 1 : 0;
     s32[u] = f && !c.diff ? closeness32(c, x) : __int_as_float(0x7fc00000);
     s64[u] = f && !c.diff ? score64(c.method, c.C, c.W, c.L1, c.norm, c.Ap, c.An, c.Td, x)
                           : __longlong_as_double(0x7ff8000000000000ll);
-    for (int v = 0; v < c.C; ++v) crit[(int64_t)u * c.C + v] = x[v];
   }
   if (c.diff) {
     diff_scores<B>(s, I);
@@ -1921,6 +2033,16 @@ __global__ void __launch_bounds__(B, 1) k_rank(const InstDev* __restrict__ inst,
       s64[u] = I.dx_pg[p];
       s32[u] = (float)I.dx_pg[p];
     }
+  }
+  if (c.fit) {
+    // viable hosts under the capacity-only rule
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int n = 0;
+      for (int u = 0; u < c.H; ++u) n += feas[u];
+      *nviable = n;
+    }
+    return;
   }
   if (threadIdx.x == 0) *nviable = c.n;
 }

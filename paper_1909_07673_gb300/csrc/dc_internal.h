@@ -184,6 +184,15 @@ int launch_rank(int block, const InstDev* d_inst, int32_t req, int32_t pod, cons
                 int32_t* feas, float* s32, double* s64, int32_t* crit, int32_t* nviable,
                 size_t smem, void* stream);
 int launch_weights(int C, int rule, const double* d_W, double* d_L1, void* stream);
+// utilities of request r (n = its containers + links) into u_c / u_e; sums
+// over requests [0, R) (u_c / u_e: per-container / per-link scratch in
+// output order, part: [4R] scratch, out: [4]); fragmentation of a state
+// (out: [4])
+int launch_utilities(const InstDev* d_inst, int r, int n, double* u_c, double* u_e, void* stream);
+int launch_utility_sums(const InstDev* d_inst, int R, double* u_c, double* u_e, double* part,
+                        double* out, void* stream);
+int launch_fragmentation(const int32_t* ctr, const int32_t* pre, const int32_t* res, int H,
+                         int link_mbps, double* out, void* stream);
 int launch_recip_table(unsigned long long* d_tab, void* stream);
 
 }  // namespace dcs

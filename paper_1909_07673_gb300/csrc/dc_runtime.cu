@@ -323,7 +323,7 @@ int validate_config(const dc_config* c) {
     return DC_E_INVAL;
   if (c->link_mbps < 0 || c->link_mbps > (1 << 21) - 1) return DC_E_INVAL;
   if (c->n_criteria != 4 && c->n_criteria != 6) return DC_E_INVAL;
-  if (c->method != DC_TOPSIS && c->method != DC_AHP) return DC_E_INVAL;
+  if (c->method < DC_TOPSIS || c->method > DC_WF) return DC_E_INVAL;
   if (c->pair_rule != DC_PAIR_RATIO && c->pair_rule != DC_PAIR_DIFF) return DC_E_INVAL;
   double s = 0.0;
   for (int v = 0; v < c->n_criteria; ++v) {
@@ -1245,10 +1245,103 @@ int dc_query_state(dc_t* d, int32_t field, int32_t* out, int64_t len) {
   return DC_OK;
 }
 
+int dc_fragmentation(dc_t* d, int64_t* active_servers, int64_t* active_links, double* f_servers,
+                     double* f_links) {
+  if (!d) return DC_E_INVAL;
+  settle(d, true);
+  cudaStream_t st = d->stream;
+  double* d_out = nullptr;
+  double h[4] = {0, 0, 0, 0};
+  if (cudaMallocAsync((void**)&d_out, 4 * sizeof(double), st) != cudaSuccess) return DC_E_NOMEM;
+  const size_t H = (size_t)d->H;
+  int rc = launch_fragmentation(d->d_state + 2 * H, d->d_state + 3 * H, d->d_state + 4 * H, d->H,
+                                d->cfg.link_mbps, d_out, st);
+  if (rc == DC_OK) rc = cuda_rc(cudaMemcpyAsync(h, d_out, sizeof(h), cudaMemcpyDeviceToHost, st));
+  cudaFreeAsync(d_out, st);
+  if (rc == DC_OK) rc = cuda_rc(cudaStreamSynchronize(st));
+  if (rc != DC_OK) return rc;
+  if (active_servers) *active_servers = (int64_t)h[0];
+  if (active_links) *active_links = (int64_t)h[1];
+  if (f_servers) *f_servers = h[2];
+  if (f_links) *f_links = h[3];
+  return DC_OK;
+}
+
+// requests [0, n) whose results are on the device (scheduled by a launch
+// that completed)
+static size_t scheduled_prefix(dc_t* d) {
+  settle(d, true);
+  size_t n = 0;
+  while (n < d->reqs.n && d->launch_of[n] != 0 && d->launch_of[n] <= d->collected_launch) ++n;
+  return n;
+}
+
+int dc_utilities(dc_t* d, int64_t req_id, double* u_container, double* u_link) {
+  if (!d) return DC_E_INVAL;
+  if (req_id < 0 || (size_t)req_id >= d->reqs.n) return DC_E_NOTFOUND;
+  settle(d, true);
+  const int64_t id = d->launch_of[req_id];
+  if (id == 0 || id > d->collected_launch) return DC_E_BUSY;
+  const ReqRec q = d->reqs.p[req_id];
+  if ((q.n_c && !u_container) || (q.n_e && !u_link)) return DC_E_INVAL;
+  cudaStream_t st = d->stream;
+  InstDev I = make_desc(d, nullptr, 0, nullptr);
+  InstDev* d_desc = nullptr;
+  double* d_u = nullptr;
+  const size_t nu = (size_t)q.n_c + (size_t)q.n_e;
+  int rc = DC_OK;
+  if (cudaMallocAsync((void**)&d_desc, sizeof(InstDev), st) != cudaSuccess ||
+      cudaMallocAsync((void**)&d_u, std::max<size_t>(1, nu) * sizeof(double), st) != cudaSuccess)
+    rc = DC_E_NOMEM;
+  if (rc == DC_OK) rc = cuda_rc(cudaMemcpyAsync(d_desc, &I, sizeof(I), cudaMemcpyHostToDevice, st));
+  if (rc == DC_OK) rc = launch_utilities(d_desc, (int)req_id, (int)nu, d_u, d_u + q.n_c, st);
+  if (rc == DC_OK && q.n_c)
+    rc = cuda_rc(cudaMemcpyAsync(u_container, d_u, q.n_c * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (rc == DC_OK && q.n_e)
+    rc = cuda_rc(cudaMemcpyAsync(u_link, d_u + q.n_c, q.n_e * sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (d_desc) cudaFreeAsync(d_desc, st);
+  if (d_u) cudaFreeAsync(d_u, st);
+  const int rc2 = cuda_rc(cudaStreamSynchronize(st));
+  return rc != DC_OK ? rc : rc2;
+}
+
+int dc_utility_summary(dc_t* d, double* sum_u_container, int64_t* n_containers,
+                       double* sum_u_link, int64_t* n_links) {
+  if (!d) return DC_E_INVAL;
+  const size_t R = scheduled_prefix(d);
+  cudaStream_t st = d->stream;
+  InstDev I = make_desc(d, nullptr, 0, nullptr);
+  InstDev* d_desc = nullptr;
+  double *d_uc = nullptr, *d_ue = nullptr, *d_part = nullptr, *d_out = nullptr;
+  const int64_t nc = R ? d->reqs.p[R - 1].c_off + d->reqs.p[R - 1].n_c : 0;
+  const int64_t ne = R ? d->reqs.p[R - 1].e_off + d->reqs.p[R - 1].n_e : 0;
+  double h[4] = {0, 0, 0, 0};
+  int rc = DC_OK;
+  if (cudaMallocAsync((void**)&d_desc, sizeof(InstDev), st) != cudaSuccess ||
+      cudaMallocAsync((void**)&d_uc, std::max<int64_t>(1, nc) * sizeof(double), st) != cudaSuccess ||
+      cudaMallocAsync((void**)&d_ue, std::max<int64_t>(1, ne) * sizeof(double), st) != cudaSuccess ||
+      cudaMallocAsync((void**)&d_part, std::max<size_t>(1, R) * 4 * sizeof(double), st) != cudaSuccess ||
+      cudaMallocAsync((void**)&d_out, 4 * sizeof(double), st) != cudaSuccess)
+    rc = DC_E_NOMEM;
+  if (rc == DC_OK) rc = cuda_rc(cudaMemcpyAsync(d_desc, &I, sizeof(I), cudaMemcpyHostToDevice, st));
+  if (rc == DC_OK) rc = launch_utility_sums(d_desc, (int)R, d_uc, d_ue, d_part, d_out, st);
+  if (rc == DC_OK) rc = cuda_rc(cudaMemcpyAsync(h, d_out, sizeof(h), cudaMemcpyDeviceToHost, st));
+  for (void* ptr : {(void*)d_desc, (void*)d_uc, (void*)d_ue, (void*)d_part, (void*)d_out})
+    if (ptr) cudaFreeAsync(ptr, st);
+  const int rc2 = cuda_rc(cudaStreamSynchronize(st));
+  if (rc != DC_OK) return rc;
+  if (rc2 != DC_OK) return rc2;
+  if (sum_u_container) *sum_u_container = h[0];
+  if (sum_u_link) *sum_u_link = h[1];
+  if (n_containers) *n_containers = (int64_t)h[2];
+  if (n_links) *n_links = (int64_t)h[3];
+  return DC_OK;
+}
+
 int dc_set_launch(int32_t k, int32_t n_criteria, int32_t method, int32_t pair_rule,
                   int32_t block, int32_t ncta) {
   if (k < 2 || k > kMaxK || (k & 1) || (n_criteria != 4 && n_criteria != 6) ||
-      (method != DC_TOPSIS && method != DC_AHP) ||
+      method < DC_TOPSIS || method > DC_WF ||
       (pair_rule != DC_PAIR_RATIO && pair_rule != DC_PAIR_DIFF))
     return DC_E_INVAL;
   const auto key = launch_key(k, n_criteria, method, pair_rule);

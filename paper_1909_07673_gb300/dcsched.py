@@ -15,7 +15,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libdcsched.so")
 
-TOPSIS, AHP = 0, 1
+TOPSIS, AHP, BF, WF = 0, 1, 2, 3
 RATIO, DIFF = 0, 1
 PENDING, ACCEPTED, REJECTED = 0, 1, 2
 SCHED_SYNC, SCHED_ASYNC = 0, 1
@@ -109,6 +109,9 @@ def lib():
         L.dc_plan_stats.argtypes = [C.c_void_p, _i64p, _i64p, _i32p, _i64p]
         L.dc_plan_destroy.argtypes = [C.c_void_p]
         L.dc_plan_destroy.restype = None
+        L.dc_utilities.argtypes = [C.c_void_p, C.c_int64, _f64p, _f64p]
+        L.dc_utility_summary.argtypes = [C.c_void_p, _f64p, _i64p, _f64p, _i64p]
+        L.dc_fragmentation.argtypes = [C.c_void_p, _i64p, _i64p, _f64p, _f64p]
         L.dc_set_launch.argtypes = [C.c_int32] * 6
         L.dc_get_launch.argtypes = [C.c_void_p, _i32p, _i32p, _i64p]
         L.dc_autotune.argtypes = [C.POINTER(C.c_void_p), C.c_int32, C.c_int32,
@@ -219,6 +222,34 @@ class DataCenter:
         _check(lib().dc_submit_batch(self.h, len(reqs), arr, _p(ids, _i64p)), "dc_submit_batch")
         self._reqs.extend(reqs)
         return int(ids[0])
+
+    def utilities(self, req_id: int):
+        """(U(i) per container, U(ij) per link) of a scheduled request
+        (Eqs. 1-2, dc_utilities)."""
+        r = self._reqs[req_id]
+        uc = np.zeros(len(r.a["pod"]), np.float64)
+        ue = np.zeros(len(r.a["src"]), np.float64)
+        _check(lib().dc_utilities(self.h, req_id, _p(uc, _f64p), _p(ue, _f64p)), "dc_utilities")
+        return uc, ue
+
+    def utility_summary(self) -> Dict[str, float]:
+        """Sums of U(i) / U(ij) over the accepted requests scheduled so far and
+        the numbers of containers / links (dc_utility_summary)."""
+        a, b = C.c_double(), C.c_double()
+        n, m = C.c_int64(), C.c_int64()
+        _check(lib().dc_utility_summary(self.h, C.byref(a), C.byref(n), C.byref(b), C.byref(m)),
+               "dc_utility_summary")
+        return {"sum_u_container": a.value, "n_containers": n.value, "sum_u_link": b.value,
+                "n_links": m.value}
+
+    def fragmentation(self):
+        """(active servers, active links, F(N^s), F(E^s)) of the current state
+        (dc_fragmentation)."""
+        a, b = C.c_int64(), C.c_int64()
+        fs, fl = C.c_double(), C.c_double()
+        _check(lib().dc_fragmentation(self.h, C.byref(a), C.byref(b), C.byref(fs), C.byref(fl)),
+               "dc_fragmentation")
+        return a.value, b.value, fs.value, fl.value
 
     def io_stats(self):
         a, b = C.c_int64(), C.c_int64()

@@ -31,7 +31,7 @@ from typing import Dict, List, Optional, Sequence, Tuple
 
 import numpy as np
 
-TOPSIS, AHP = 0, 1
+TOPSIS, AHP, BF, WF = 0, 1, 2, 3
 RATIO, DIFF = 0, 1
 
 # Table IV weighting schemes for the four criteria (CPU, RAM, fragmentation,
