@@ -74,6 +74,9 @@ def parse():
                     help="only the k=48 data-center measurement (one JSON line)")
     ap.add_argument("--no-comparators", action="store_true",
                     help="skip the method comparison (TOPSIS, AHP, best fit, worst fit)")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="skip the general-graph widest-shortest-path measurement")
+    ap.add_argument("--graph-pairs", type=int, default=2048)
     return ap.parse_args()
 
 
@@ -368,6 +371,55 @@ def run_comparators(args, ds, torch):
             "methods": out}
 
 
+# ----------------------------------------------------------------- general graphs
+
+def run_graph_paths(args, ds, torch, peak):
+    """Widest shortest paths between random host pairs of the k=48 fat-tree
+    taken as a general graph (30,528 nodes, 82,944 links, residuals
+    U[0, 1) x 40 Gbps pre-load), through dc_graph_widest_paths (host arrays
+    in and out); the oracle's search timed on a sample of the pairs."""
+    import oracle as O
+
+    k, H = 48, 48 ** 3 // 4
+    rng = np.random.default_rng(48)
+    res = (40000 - np.floor(rng.random(3 * H) * 40000)).astype(np.int32)
+    V, lu, lv = O.fattree_graph(k, res)
+    pairs = rng.integers(0, H, (args.graph_pairs, 2)).astype(np.int32)
+    g = ds.Graph(V, lu, lv, res)
+    g.widest_paths(pairs[:64, 0], pairs[:64, 1], 8)  # warm-up
+    times = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        hops, bott, links = g.widest_paths(pairs[:, 0], pairs[:, 1], 8)
+        times.append(time.perf_counter() - t)
+    g.close()
+    sec = min(times)
+    # algorithmic bytes of one pair: two breadth-first passes, each reading
+    # every adjacency entry (neighbour, link, residual, label: 16 B) and
+    # writing / reading every node's two labels and queue slot (16 B)
+    bytes_pair = 2 * (16 * 2 * len(lu) + 16 * V)
+    gbs = args.graph_pairs * bytes_pair / sec / 1e9
+    og = O.OracleGraph(V, lu, lv, res)
+    t = time.perf_counter()
+    n_or = 0
+    while n_or < args.graph_pairs and time.perf_counter() - t < 5.0:
+        og.widest_path(int(pairs[n_or, 0]), int(pairs[n_or, 1]))
+        n_or += 1
+    osec = time.perf_counter() - t
+    return {
+        "workload": "k=48 fat-tree as a general graph (%d nodes, %d links), %d random host "
+                    "pairs" % (V, len(lu), args.graph_pairs),
+        "pairs_per_s": args.graph_pairs / sec, "ms_per_call": sec * 1e3,
+        "note": "wall time of dc_graph_widest_paths (pairs in, hops / bottleneck / links "
+                "out through host memory)",
+        "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                     "frac": gbs / peak, "bytes_per_pair": bytes_pair},
+        "cpu_oracle": {"pairs_per_s": n_or / osec, "cores": 1,
+                       "sample": "first %d pairs, one thread" % n_or},
+    }
+
+
 # ----------------------------------------------------------------- largest fat-tree
 
 def run_largest(args, ds, torch, peak):
@@ -551,6 +603,7 @@ def run_ours(args):
     traffic = ncu_traffic(hr)
     largest = None if args.no_largest else run_largest(args, ds, torch, peak)
     comparators = None if (args.no_comparators or rank != 0) else run_comparators(args, ds, torch)
+    graph = None if (args.no_graph or rank != 0) else run_graph_paths(args, ds, torch, peak)
     if rank != 0:
         if dist:
             dist.barrier()
@@ -563,10 +616,12 @@ def run_ours(args):
     if tuned is not None:
         cfg["launch_shapes"] = [
             {"k": e["k"], "block": e["block"], "blocks_per_dc": e["ncta"],
-             "default": [e["block0"], e["ncta0"]], "trials": e["trials"]} for e in tuned]
+             "default": [e["block0"], e["ncta0"]], "trials": e["trials"],
+             "kept_after_full_check": e["kept"]} for e in tuned]
         cfg["autotune"] = ("coordinate descent over launch shapes per fat-tree size, each "
                            "trial a state-resetting launch of the first %d operations of every "
-                           "data center" % args.tune_ops)
+                           "data center; the result is kept only if faster than the starting "
+                           "shapes on all operations" % args.tune_ops)
     line = {
         "metric": METRIC, "value": hr_all / (ms_step * 1e-3), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
@@ -602,6 +657,8 @@ def run_ours(args):
         line["largest_fat_tree"] = largest
     if comparators is not None:
         line["comparators"] = comparators
+    if graph is not None:
+        line["graph_paths"] = graph
     print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

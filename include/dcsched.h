@@ -249,6 +249,29 @@ int dc_utility_summary(dc_t* dc, double* sum_u_container, int64_t* n_containers,
 int dc_fragmentation(dc_t* dc, int64_t* active_servers, int64_t* active_links,
                      double* f_servers, double* f_links);
 
+/* --- general data-center graphs (Sec. V-D) ----------------------------------
+ * The widest shortest path between two servers on an arbitrary undirected
+ * graph (the paper's modified Dijkstra, one search per (source, destination)
+ * pair in one kernel), for data centers that are not fat-trees.  Links l =
+ * 0..n_links-1 join link_u[l] != link_v[l] (nodes 0..n_nodes-1, at most one
+ * link between two nodes) with residual bandwidth residual[l] >= 0; the
+ * graph copies them to the device (dc_graph_set_residual replaces the
+ * residuals).  For each pair: the fewest hops, then the largest bottleneck
+ * (smallest residual on the path), then the lexicographically smallest
+ * sequence of node ids from the source; hops[p] = -1 and bottleneck[p] = -1
+ * when the destination is unreachable, hops 0 and bottleneck INT32_MAX when
+ * source = destination.  links[p * max_hops + i] receives the i-th link id of
+ * the path (the first max_hops links; -1 beyond the path).  Host arrays,
+ * caller-allocated; blocking.  DC_E_INVAL for invalid links or node ids. */
+typedef struct dc_graph dc_graph;
+int dc_graph_create(int32_t n_nodes, int32_t n_links, const int32_t* link_u,
+                    const int32_t* link_v, const int32_t* residual, void* cuda_stream,
+                    dc_graph** out);
+void dc_graph_destroy(dc_graph* g);
+int dc_graph_set_residual(dc_graph* g, const int32_t* residual);
+int dc_graph_widest_paths(dc_graph* g, int32_t n_pairs, const int32_t* src, const int32_t* dst,
+                          int32_t max_hops, int32_t* hops, int32_t* bottleneck, int32_t* links);
+
 /* --- launch shapes --------------------------------------------------------
  * No counterpart in the paper (a GPU launch parameter).  The scheduling
  * kernel of a plan runs one thread block of `block` threads per data center
@@ -283,7 +306,9 @@ int dc_get_launch(const dc_t* dc, int32_t* block, int32_t* ncta, int64_t* smem_b
  * instances, best of two after a warm-up, the other kinds keeping their
  * current shapes; a candidate replaces the current shape when it is at
  * least 3 % faster.  Only the first max_ops operations of every instance
- * run in a trial (0: all).  Blocking.  The instances' state and queues are
+ * run in a trial (0: all); the shapes found that way are then timed on all
+ * queued operations against the starting shapes and kept only when at least
+ * 1 % faster.  Blocking.  The instances' state and queues are
  * as before the call (their device state is saved and restored).  Writes
  * one entry per kind, up to max_out, and the number of kinds to *n_out. */
 typedef struct {
@@ -291,7 +316,8 @@ typedef struct {
   int32_t block, ncta;    /* chosen shape */
   int32_t block0, ncta0;  /* shape before tuning */
   int32_t trials;         /* candidate shapes timed */
-  int32_t pad;
+  int32_t kept;           /* 1: kept after the check on all operations, 0: the
+                             starting shapes were restored, -1: no check */
   double ms;              /* launch time with the chosen shape (ms) */
   double ms0;             /* launch time before this kind was tuned (ms) */
 } dc_tune_entry;

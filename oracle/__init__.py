@@ -86,6 +86,13 @@ def lib():
         L.orc_utilities.restype = None
         L.orc_fragmentation.argtypes = [C.c_void_p, _i64p, _i64p, _f64p, _f64p]
         L.orc_fragmentation.restype = None
+        L.orc_graph_create.argtypes = [C.c_int32, C.c_int32, _i32p, _i32p, _i32p,
+                                       C.POINTER(C.c_void_p)]
+        L.orc_graph_destroy.argtypes = [C.c_void_p]
+        L.orc_graph_destroy.restype = None
+        L.orc_graph_widest_path.argtypes = [C.c_void_p, C.c_int32, C.c_int32, _i32p, _i32p,
+                                            _i32p, C.c_int32]
+        L.orc_graph_widest_path.restype = C.c_int32
     return _lib
 
 
@@ -210,6 +217,62 @@ class OracleDC:
         if F < 0:
             raise ValueError("orc_rank_pod failed: %d" % F)
         return feas.astype(bool), crit.reshape(self.H, self.n_criteria), score
+
+
+class OracleGraph:
+    """Undirected graph with per-link residual bandwidth (orc_graph)."""
+
+    def __init__(self, n_nodes: int, lu, lv, res):
+        self.V = int(n_nodes)
+        self.lu = np.ascontiguousarray(lu, np.int32)
+        self.lv = np.ascontiguousarray(lv, np.int32)
+        self.res = np.ascontiguousarray(res, np.int32)
+        h = C.c_void_p()
+        rc = lib().orc_graph_create(self.V, len(self.lu), _p(self.lu, _i32p), _p(self.lv, _i32p),
+                                    _p(self.res, _i32p), C.byref(h))
+        if rc != 0:
+            raise ValueError("orc_graph_create failed: %d" % rc)
+        self.h = h
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.orc_graph_destroy(self.h)
+            self.h = None
+
+    def widest_path(self, s: int, t: int, max_nodes: int = 64):
+        """(hops, bottleneck, nodes, links); hops -1 when unreachable."""
+        b = C.c_int32()
+        nodes = np.full(max_nodes, -1, np.int32)
+        links = np.full(max_nodes, -1, np.int32)
+        h = lib().orc_graph_widest_path(self.h, s, t, C.byref(b), _p(nodes, _i32p),
+                                        _p(links, _i32p), max_nodes)
+        if h < 0:
+            return -1, -1, nodes[:0], links[:0]
+        return h, b.value, nodes[:h + 1], links[:h]
+
+
+def fattree_graph(k: int, res):
+    """A k-port fat-tree as a general graph: nodes hosts [0, H), edge switches
+    [H, H + E), aggregation switches [H + E, H + 2E) numbered pod * k/2 + a,
+    core switches [H + 2E, ...) numbered a * k/2 + c; link ids are those of
+    the fat-tree numbering (host links, edge-aggregation, aggregation-core).
+    Returns (n_nodes, lu, lv) for residuals res[3H]."""
+    half = k // 2
+    H, E = k ** 3 // 4, k * k // 2
+    lu = np.zeros(3 * H, np.int32)
+    lv = np.zeros(3 * H, np.int32)
+    for h in range(H):
+        lu[h], lv[h] = h, H + h // half
+    for e in range(E):
+        p = e // half
+        for a in range(half):
+            lu[H + e * half + a], lv[H + e * half + a] = H + e, H + E + p * half + a
+    for p in range(k):
+        for a in range(half):
+            for c in range(half):
+                l = 2 * H + (p * half + a) * half + c
+                lu[l], lv[l] = H + E + p * half + a, H + 2 * E + a * half + c
+    return H + 2 * E + half * half, lu, lv
 
 
 def utilities(q: Dict[str, np.ndarray], out: Dict[str, np.ndarray]):

@@ -912,3 +912,151 @@ void orc_fragmentation(const orc_dc* d, int64_t* act_s, int64_t* act_l, double* 
   if (f_s) *f_s = (double)ns / (double)d->H;
   if (f_l) *f_l = (double)nl / (double)d->L;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Widest shortest paths on a general graph [Sec. V-D].  Steps: breadth-first
+ * hop distances from s and from t; the widest bottleneck over the shortest
+ * s -> v paths, layer by layer from s (and likewise towards t); then a walk
+ * from s that takes, at each hop, the smallest-id neighbour that stays on a
+ * shortest s -> t path and keeps every link of the rest of the path at or
+ * above the optimal bottleneck.  Readings: the paper gives no tie rule; the
+ * smallest node sequence reproduces, on a fat-tree numbered hosts, edge,
+ * aggregation (pod-major), core (aggregation-major), the lowest aggregation
+ * then lowest core rule of the fat-tree paths above. */
+struct orc_graph {
+  int32_t V, L;
+  int32_t *off, *nbr, *lnk;  /* adjacency: neighbours and link ids of node v in off[v]..off[v+1] */
+  int32_t* res;
+};
+
+int orc_graph_create(int32_t V, int32_t L, const int32_t* lu, const int32_t* lv,
+                     const int32_t* res, orc_graph** out) {
+  *out = NULL;
+  if (V <= 0 || L < 0) return ORC_EINVAL;
+  for (int32_t l = 0; l < L; ++l)
+    if (lu[l] < 0 || lu[l] >= V || lv[l] < 0 || lv[l] >= V || lu[l] == lv[l] || res[l] < 0)
+      return ORC_EINVAL;
+  orc_graph* g = (orc_graph*)calloc(1, sizeof(orc_graph));
+  g->V = V;
+  g->L = L;
+  g->off = (int32_t*)calloc((size_t)V + 1, sizeof(int32_t));
+  g->nbr = (int32_t*)malloc(sizeof(int32_t) * (2 * (size_t)L + 1));
+  g->lnk = (int32_t*)malloc(sizeof(int32_t) * (2 * (size_t)L + 1));
+  g->res = (int32_t*)malloc(sizeof(int32_t) * ((size_t)L + 1));
+  for (int32_t l = 0; l < L; ++l) {
+    g->off[lu[l] + 1] += 1;
+    g->off[lv[l] + 1] += 1;
+    g->res[l] = res[l];
+  }
+  for (int32_t v = 0; v < V; ++v) g->off[v + 1] += g->off[v];
+  int32_t* fill = (int32_t*)calloc((size_t)V, sizeof(int32_t));
+  for (int32_t l = 0; l < L; ++l) {
+    const int32_t a = lu[l], b = lv[l];
+    g->nbr[g->off[a] + fill[a]] = b;
+    g->lnk[g->off[a] + fill[a]++] = l;
+    g->nbr[g->off[b] + fill[b]] = a;
+    g->lnk[g->off[b] + fill[b]++] = l;
+  }
+  free(fill);
+  /* no duplicate link between two nodes */
+  for (int32_t v = 0; v < V; ++v)
+    for (int32_t i = g->off[v]; i < g->off[v + 1]; ++i)
+      for (int32_t j = i + 1; j < g->off[v + 1]; ++j)
+        if (g->nbr[i] == g->nbr[j]) {
+          orc_graph_destroy(g);
+          return ORC_EINVAL;
+        }
+  *out = g;
+  return ORC_OK;
+}
+
+void orc_graph_destroy(orc_graph* g) {
+  if (!g) return;
+  free(g->off);
+  free(g->nbr);
+  free(g->lnk);
+  free(g->res);
+  free(g);
+}
+
+/* hop distances from r (-1 unreachable) and the widest bottleneck over the
+ * shortest r -> v paths (INT32_MAX at r) */
+static void graph_layers(const orc_graph* g, int32_t r, int32_t* dist, int32_t* width,
+                         int32_t* queue) {
+  for (int32_t v = 0; v < g->V; ++v) {
+    dist[v] = -1;
+    width[v] = -1;
+  }
+  dist[r] = 0;
+  width[r] = INT32_MAX;
+  int32_t head = 0, tail = 0;
+  queue[tail++] = r;
+  while (head < tail) {
+    const int32_t v = queue[head++];
+    for (int32_t i = g->off[v]; i < g->off[v + 1]; ++i) {
+      const int32_t n = g->nbr[i];
+      if (dist[n] < 0) {
+        dist[n] = dist[v] + 1;
+        queue[tail++] = n;
+      }
+    }
+  }
+  /* widths in breadth-first order: every predecessor of v comes before v */
+  for (int32_t q = 1; q < tail; ++q) {
+    const int32_t v = queue[q];
+    int32_t best = -1;
+    for (int32_t i = g->off[v]; i < g->off[v + 1]; ++i) {
+      const int32_t p = g->nbr[i];
+      if (dist[p] == dist[v] - 1) {
+        const int32_t w = min2(width[p], g->res[g->lnk[i]]);
+        if (w > best) best = w;
+      }
+    }
+    width[v] = best;
+  }
+}
+
+int32_t orc_graph_widest_path(const orc_graph* g, int32_t s, int32_t t, int32_t* bottleneck,
+                              int32_t* nodes, int32_t* links, int32_t max_nodes) {
+  if (s < 0 || s >= g->V || t < 0 || t >= g->V) return -1;
+  if (s == t) {
+    if (bottleneck) *bottleneck = INT32_MAX;
+    if (nodes && max_nodes >= 1) nodes[0] = s;
+    return 0;
+  }
+  int32_t* ds = (int32_t*)malloc(sizeof(int32_t) * g->V);
+  int32_t* ws = (int32_t*)malloc(sizeof(int32_t) * g->V);
+  int32_t* dt = (int32_t*)malloc(sizeof(int32_t) * g->V);
+  int32_t* wt = (int32_t*)malloc(sizeof(int32_t) * g->V);
+  int32_t* queue = (int32_t*)malloc(sizeof(int32_t) * g->V);
+  graph_layers(g, s, ds, ws, queue);
+  graph_layers(g, t, dt, wt, queue);
+  const int32_t D = ds[t];
+  if (D < 0) {
+    free(ds); free(ws); free(dt); free(wt); free(queue);
+    return -1;
+  }
+  const int32_t W = ws[t];
+  if (bottleneck) *bottleneck = W;
+  int32_t cur = s;
+  if (nodes && max_nodes >= D + 1) nodes[0] = s;
+  for (int32_t h = 1; h <= D; ++h) {
+    int32_t next = -1, via = -1;
+    for (int32_t i = g->off[cur]; i < g->off[cur + 1]; ++i) {
+      const int32_t n = g->nbr[i];
+      if (ds[n] != h || dt[n] != D - h) continue;    /* on a shortest s -> t path */
+      if (g->res[g->lnk[i]] < W || wt[n] < W) continue; /* keeps the bottleneck */
+      if (next < 0 || n < next) {
+        next = n;
+        via = g->lnk[i];
+      }
+    }
+    if (nodes && max_nodes >= D + 1) {
+      nodes[h] = next;
+      if (links) links[h - 1] = via;
+    }
+    cur = next;
+  }
+  free(ds); free(ws); free(dt); free(wt); free(queue);
+  return D;
+}

@@ -126,6 +126,22 @@ void orc_utilities(const orc_request* req, const orc_result* res, double* u_cont
  * be NULL. */
 void orc_fragmentation(const orc_dc* dc, int64_t* active_servers, int64_t* active_links,
                        double* f_servers, double* f_links);
+/* Widest shortest paths on a general undirected graph [Sec. V-D: the modified
+ * Dijkstra that finds, between two servers, the shortest path with the most
+ * available bandwidth; its links are stored once, u < v].  Links l = 0..L-1
+ * join lu[l] and lv[l] (distinct nodes, no duplicate link) and have the
+ * residual bandwidth res[l] >= 0.  For a pair (s, t): the fewest hops first,
+ * then the largest bottleneck (smallest residual along the path), then the
+ * lexicographically smallest sequence of node ids from s.  Returns the hops
+ * (0 for s = t, -1 when t is unreachable) and writes the bottleneck
+ * (INT32_MAX for s = t), the nodes [hops + 1] and the links [hops] when
+ * hops + 1 <= max_nodes. */
+typedef struct orc_graph orc_graph;
+int orc_graph_create(int32_t n_nodes, int32_t n_links, const int32_t* lu, const int32_t* lv,
+                     const int32_t* res, orc_graph** out);
+void orc_graph_destroy(orc_graph* g);
+int32_t orc_graph_widest_path(const orc_graph* g, int32_t s, int32_t t, int32_t* bottleneck,
+                              int32_t* nodes, int32_t* links, int32_t max_nodes);
 /* Scoring primitives over a viable-host matrix x[F * C] (row-major per host). */
 void orc_topsis(int32_t F, int32_t C, const int64_t* x, const double* W, double* cl);
 void orc_ahp_weights(int32_t C, const double* W, int32_t rule, double* L1);

@@ -757,8 +757,9 @@ static __device__ void column_stats(const Sm& s) {
       }
     }
   };
-  // a global state: two hosts in flight hide part of the L2 latency
-  if (CL || c.gstate) {
+  // the cluster kernel (global state): two hosts in flight hide part of the
+  // L2 latency; the one-block kernel runs faster without unrolling
+  if (CL) {
 #pragma unroll 2
     for (int u = c.h0 + tid; u < c.h1; u += B) visit(u);
   } else {
@@ -1100,7 +1101,7 @@ static __device__ void pick_host(const Sm& s) {
       me.m2 = fmaxf(me.m2, sc);
     }
   };
-  if (CL || c.gstate) {
+  if (CL) {
 #pragma unroll 2
     for (int u = c.h0 + tid; u < c.h1; u += B) visit(u);
   } else {

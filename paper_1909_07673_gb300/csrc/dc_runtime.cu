@@ -1046,16 +1046,20 @@ int dc_autotune(dc_t* const* dcs, int32_t n, int32_t max_ops, dc_tune_entry* out
   if (rc == DC_OK) rc = cuda_rc(cudaEventCreate(&e1));
   double best = 0;
   if (rc == DC_OK) rc = time_plan(dcs, n, lim, cur, e0, e1, &best);
-  int32_t written = 0;
+  const std::vector<LaunchCfg> initial = cur;
+  std::vector<LaunchCfg> before(kinds.size());
+  std::vector<double> ms0(kinds.size(), 0.0);
+  std::vector<int> ntrial(kinds.size(), 0);
   for (size_t q = 0; q < kinds.size() && rc == DC_OK; ++q) {
     Kind& kd = kinds[q];
+    before[q] = cur[kd.members[0]];
     if (kd.work <= 0) continue;
-    const LaunchCfg before = cur[kd.members[0]];
-    const double ms0 = best;
-    LaunchCfg chosen = before;
+    const LaunchCfg before_q = cur[kd.members[0]];
+    const double ms0_q = best;
+    LaunchCfg chosen = before_q;
     int trials = 0;
     for (const LaunchCfg& L : kd.cands) {
-      if (same_shape(L, before)) continue;
+      if (same_shape(L, before_q)) continue;
       std::vector<LaunchCfg> sh = cur;
       for (int i : kd.members) sh[i] = L;
       double t = 0;
@@ -1069,6 +1073,30 @@ int dc_autotune(dc_t* const* dcs, int32_t n, int32_t max_ops, dc_tune_entry* out
     }
     if (rc != DC_OK) break;
     for (int i : kd.members) cur[i] = chosen;
+    before[q] = before_q;
+    ms0[q] = ms0_q;
+    ntrial[q] = trials;
+  }
+  // the trials ran a prefix of the operations: keep the tuned shapes only if
+  // they are faster than the starting ones on the whole queued work
+  double full_tuned = 0, full_initial = 0;
+  bool changed = false;
+  int32_t kept = -1;
+  for (int32_t i = 0; i < n; ++i) changed = changed || !same_shape(cur[i], initial[i]);
+  if (rc == DC_OK && changed && lim != SIZE_MAX) {
+    rc = time_plan(dcs, n, SIZE_MAX, cur, e0, e1, &full_tuned);
+    if (rc == DC_OK) rc = time_plan(dcs, n, SIZE_MAX, initial, e0, e1, &full_initial);
+    kept = 1;
+    if (rc == DC_OK && !(full_tuned < 0.99 * full_initial)) {
+      cur = initial;
+      kept = 0;
+    }
+  }
+  int32_t written = 0;
+  for (size_t q = 0; q < kinds.size() && rc == DC_OK; ++q) {
+    const Kind& kd = kinds[q];
+    if (kd.work <= 0) continue;
+    const LaunchCfg chosen = cur[kd.members[0]];
     {
       std::lock_guard<std::mutex> lk(g_launch_mu);
       g_launch[kd.key] = std::make_pair(chosen.block, chosen.ncta);
@@ -1081,11 +1109,12 @@ int dc_autotune(dc_t* const* dcs, int32_t n, int32_t max_ops, dc_tune_entry* out
       e.pair_rule = std::get<3>(kd.key);
       e.block = chosen.block;
       e.ncta = chosen.ncta;
-      e.block0 = before.block;
-      e.ncta0 = before.ncta;
-      e.trials = trials;
+      e.block0 = before[q].block;
+      e.ncta0 = before[q].ncta;
+      e.trials = ntrial[q];
+      e.kept = kept;
       e.ms = best;
-      e.ms0 = ms0;
+      e.ms0 = ms0[q];
     }
   }
   for (int32_t i = 0; i < n; ++i)

@@ -64,7 +64,7 @@ class _TuneEntry(C.Structure):
     _fields_ = [("k", C.c_int32), ("n_criteria", C.c_int32), ("method", C.c_int32),
                 ("pair_rule", C.c_int32), ("block", C.c_int32), ("ncta", C.c_int32),
                 ("block0", C.c_int32), ("ncta0", C.c_int32), ("trials", C.c_int32),
-                ("pad", C.c_int32), ("ms", C.c_double), ("ms0", C.c_double)]
+                ("kept", C.c_int32), ("ms", C.c_double), ("ms0", C.c_double)]
 
 
 _lib = None
@@ -112,6 +112,13 @@ def lib():
         L.dc_utilities.argtypes = [C.c_void_p, C.c_int64, _f64p, _f64p]
         L.dc_utility_summary.argtypes = [C.c_void_p, _f64p, _i64p, _f64p, _i64p]
         L.dc_fragmentation.argtypes = [C.c_void_p, _i64p, _i64p, _f64p, _f64p]
+        L.dc_graph_create.argtypes = [C.c_int32, C.c_int32, _i32p, _i32p, _i32p, C.c_void_p,
+                                      C.POINTER(C.c_void_p)]
+        L.dc_graph_destroy.argtypes = [C.c_void_p]
+        L.dc_graph_destroy.restype = None
+        L.dc_graph_set_residual.argtypes = [C.c_void_p, _i32p]
+        L.dc_graph_widest_paths.argtypes = [C.c_void_p, C.c_int32, _i32p, _i32p, C.c_int32,
+                                            _i32p, _i32p, _i32p]
         L.dc_set_launch.argtypes = [C.c_int32] * 6
         L.dc_get_launch.argtypes = [C.c_void_p, _i32p, _i32p, _i64p]
         L.dc_autotune.argtypes = [C.POINTER(C.c_void_p), C.c_int32, C.c_int32,
@@ -380,6 +387,48 @@ class Server:
         self.close()
 
 
+class Graph:
+    """A general data-center graph with per-link residual bandwidth on the
+    device (dc_graph); widest_paths runs the widest-shortest-path search for
+    many (source, destination) pairs in one kernel."""
+
+    def __init__(self, n_nodes: int, link_u, link_v, residual, stream=None):
+        lu = np.ascontiguousarray(link_u, np.int32)
+        lv = np.ascontiguousarray(link_v, np.int32)
+        res = np.ascontiguousarray(residual, np.int32)
+        h = C.c_void_p()
+        _check(lib().dc_graph_create(int(n_nodes), len(lu), _p(lu, _i32p), _p(lv, _i32p),
+                                     _p(res, _i32p), _stream_handle(stream), C.byref(h)),
+               "dc_graph_create")
+        self.h = h
+        self.V, self.L = int(n_nodes), len(lu)
+
+    def set_residual(self, residual) -> None:
+        res = np.ascontiguousarray(residual, np.int32)
+        _check(lib().dc_graph_set_residual(self.h, _p(res, _i32p)), "dc_graph_set_residual")
+
+    def widest_paths(self, src, dst, max_hops: int = 16):
+        """(hops, bottleneck, links[n, max_hops]) per pair."""
+        s = np.ascontiguousarray(src, np.int32)
+        d = np.ascontiguousarray(dst, np.int32)
+        n = len(s)
+        hops = np.zeros(n, np.int32)
+        bott = np.zeros(n, np.int32)
+        links = np.full(max(1, n * max_hops), -1, np.int32)
+        _check(lib().dc_graph_widest_paths(self.h, n, _p(s, _i32p), _p(d, _i32p), max_hops,
+                                           _p(hops, _i32p), _p(bott, _i32p), _p(links, _i32p)),
+               "dc_graph_widest_paths")
+        return hops, bott, links[:n * max_hops].reshape(n, max_hops)
+
+    def close(self) -> None:
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.dc_graph_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+
 def set_launch(k: int, n_criteria: int, method: int, pair_rule: int, block: int,
                ncta: int = 1) -> None:
     """Records the scheduling-kernel shape (threads per block, blocks per
@@ -397,7 +446,7 @@ def autotune(dcs: Sequence["DataCenter"], max_ops: int = 0) -> List[Dict[str, fl
     n = C.c_int32()
     _check(lib().dc_autotune(_handles(list(dcs)), len(dcs), max_ops, out, 64, C.byref(n)),
            "dc_autotune")
-    return [{f: getattr(out[i], f) for f, _ in _TuneEntry._fields_ if f != "pad"}
+    return [{f: getattr(out[i], f) for f, _ in _TuneEntry._fields_}
             for i in range(min(n.value, 64))]
 
 
