@@ -329,16 +329,16 @@ def run_serving(args, ds, torch):
 # ----------------------------------------------------------------- method comparison
 
 def run_comparators(args, ds, torch):
-    """The k=16 workload (1,024 hosts, 0-70 % pre-load, 1,000 requests of
-    4-64 containers) with [min, max] intervals, scheduled by TOPSIS, AHP and
-    the best-fit / worst-fit comparators: device time, acceptance, mean
-    utilities (Eqs. 1-2) and the final fragmentation."""
+    """The k=16 workload's requests (1,000 of 4-64 containers, [min, max]
+    intervals) on an empty k=16 fat-tree, scheduled by TOPSIS, AHP and the
+    best-fit / worst-fit comparators: device time, acceptance, mean utilities
+    (Eqs. 1-2) and the final fragmentation."""
     from paper_1909_07673_gb300 import workloads as W
 
     out = {}
     stream = torch.cuda.Stream()
     for name, method in (("TOPSIS", W.TOPSIS), ("AHP", W.AHP), ("BF", W.BF), ("WF", W.WF)):
-        inst = W.k16(method=method, intervals=True).instances[0]
+        inst = W.k16(method=method, intervals=True, preload=0.0).instances[0]
         dc = ds.load_instance(inst, stream=stream)
         plan = ds.Plan([dc], ds.PLAN_RESET)
         times = []
@@ -366,8 +366,8 @@ def run_comparators(args, ds, torch):
         }
         plan.close()
         dc.close()
-    return {"workload": "one k=16 fat-tree (1,024 hosts, 0-70 % pre-load), 1,000 requests of "
-                        "4-64 containers with [min, max] intervals, 6 criteria",
+    return {"workload": "one empty k=16 fat-tree (1,024 hosts), 1,000 requests of 4-64 "
+                        "containers with [min, max] intervals, 6 criteria",
             "methods": out}
 
 

@@ -301,12 +301,14 @@ def small(seed: int = 0, method: int = TOPSIS, pair_rule: int = RATIO,
 
 
 def k16(seed: int = 1, method: int = TOPSIS, pair_rule: int = RATIO, scheme: str = "flat",
-        n_requests: int = 1000, k: int = 16, intervals: bool = False) -> Workload:
-    """k=16 (1,024 hosts, 10 Gbps), pre-load U[0, 0.7) per host resource and
-    link, n_requests of U{4..64} containers, singleton pods, Erdos-Renyi
-    p=0.1 made connected, log-uniform 1-1000 Mbps, 6 criteria."""
+        n_requests: int = 1000, k: int = 16, intervals: bool = False,
+        preload: float = 0.7) -> Workload:
+    """k=16 (1,024 hosts, 10 Gbps), pre-load U[0, preload) per host resource
+    and link (0.7 by default; 0: an empty data center, the same requests),
+    n_requests of U{4..64} containers, singleton pods, Erdos-Renyi p=0.1 made
+    connected, log-uniform 1-1000 Mbps, 6 criteria."""
     rng = np.random.Generator(np.random.PCG64(seed))
-    pre = gen_preload(rng, k, 32, 64, 10000, 0.7)
+    pre = gen_preload(rng, k, 32, 64, 10000, preload)
     reqs = [gen_request(rng, int(rng.integers(4, 65)), p_edge=0.1, bw=_bw_loguniform(1000.0),
                         intervals=intervals) for _ in range(n_requests)]
     inst = Instance(k, 32, 64, 10000, 6, method, pair_rule, WEIGHTS[6][scheme],
