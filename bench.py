@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--no-graph", action="store_true",
                     help="skip the general-graph widest-shortest-path measurement")
     ap.add_argument("--graph-pairs", type=int, default=2048)
+    ap.add_argument("--no-simulation", action="store_true",
+                    help="skip the discrete-event simulation with queueing")
     return ap.parse_args()
 
 
@@ -371,6 +373,52 @@ def run_comparators(args, ds, torch):
             "methods": out}
 
 
+# ----------------------------------------------------------------- simulation
+
+def run_simulation(args, ds, torch):
+    """The discrete-event simulation with queueing (dc_simulate, one launch
+    per run) on the GPU evaluation's scenario (k=20 fat-tree of 24-core /
+    256 GB hosts, 1 Gbps, 6,000 four-container requests over 500 steps,
+    running times up to 250) and on a loaded one (k=8 of 8-core / 16 GB hosts,
+    200 Mbps, 2,000 requests), for TOPSIS, AHP, best fit and worst fit: wall
+    time of the call, requests started, queueing delay (steps), decisions;
+    the oracle timed on the first scenario with TOPSIS."""
+    import oracle as O
+    from paper_1909_07673_gb300 import workloads as W
+
+    scen = {"paper_k20": dict(k=20, n_requests=6000, n_steps=500, max_duration=250),
+            "loaded_k8": dict(k=8, n_requests=2000, n_steps=500, max_duration=250,
+                              host_cpu=8, host_mem=16, link_mbps=200)}
+    out = {}
+    stream = torch.cuda.Stream()
+    for name, cfg in scen.items():
+        out[name] = {"config": cfg, "methods": {}}
+        for mname, m in (("TOPSIS", W.TOPSIS), ("AHP", W.AHP), ("BF", W.BF), ("WF", W.WF)):
+            wl, sub, dur = W.simulation(method=m, **cfg)
+            inst = wl.instances[0]
+            dc = ds.load_instance(inst, stream=stream)
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            start = dc.simulate(cfg["n_steps"], sub, dur)
+            sec = time.perf_counter() - t
+            st = start >= 0
+            delay = (start - sub)[st]
+            dec = sum(dc.status(r)[1] for r in range(inst.reqs.n))
+            out[name]["methods"][mname] = {
+                "wall_s": sec, "started": int(st.sum()), "requests": int(inst.reqs.n),
+                "delay_mean": float(delay.mean()) if len(delay) else None,
+                "delay_p99": float(np.percentile(delay, 99)) if len(delay) else None,
+                "decisions": int(dec), "us_per_decision": sec * 1e6 / max(1, dec)}
+            dc.close()
+    wl, sub, dur = W.simulation(method=W.TOPSIS, **scen["paper_k20"])
+    inst = wl.instances[0]
+    odc = O.OracleDC.from_instance(inst)
+    t = time.perf_counter()
+    odc.simulate([inst.reqs.request(r) for r in range(inst.reqs.n)], sub, dur, 500)
+    out["paper_k20"]["oracle_topsis_s"] = time.perf_counter() - t
+    return out
+
+
 # ----------------------------------------------------------------- general graphs
 
 def run_graph_paths(args, ds, torch, peak):
@@ -604,6 +652,7 @@ def run_ours(args):
     largest = None if args.no_largest else run_largest(args, ds, torch, peak)
     comparators = None if (args.no_comparators or rank != 0) else run_comparators(args, ds, torch)
     graph = None if (args.no_graph or rank != 0) else run_graph_paths(args, ds, torch, peak)
+    simulation = None if (args.no_simulation or rank != 0) else run_simulation(args, ds, torch)
     if rank != 0:
         if dist:
             dist.barrier()
@@ -659,6 +708,8 @@ def run_ours(args):
         line["comparators"] = comparators
     if graph is not None:
         line["graph_paths"] = graph
+    if simulation is not None:
+        line["simulation"] = simulation
     print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

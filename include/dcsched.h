@@ -249,6 +249,25 @@ int dc_utility_summary(dc_t* dc, double* sum_u_container, int64_t* n_containers,
 int dc_fragmentation(dc_t* dc, int64_t* active_servers, int64_t* active_links,
                      double* f_servers, double* f_links);
 
+/* --- discrete-event simulation with queueing (Sec. IV-B.2, VI-A) ------------
+ * Runs the instance's queued requests (submissions only; DC_E_BUSY when a
+ * departure is queued) through a simulation of n_steps >= 1 steps in one
+ * device launch.  Request i of the queued ones (submission order) is submitted at
+ * step submit_step[i] >= 0 and runs for duration[i] >= 1 steps.  At each step
+ * t: the requests whose running time ends at t leave and their resources
+ * return; the requests submitted at t join the tail of one FCFS queue
+ * (submission step, then submission order); the queue's head is scheduled
+ * again and again (pods, ranking, commit as dc_schedule): a placed request
+ * starts at t; the first head that cannot be placed stays at the head with
+ * every request behind it and is tried again only in a later step in which a
+ * request left (on an unchanged state the attempt would fail again).
+ * start_step[i] receives the step request i started, -1 if it never did
+ * (then dc_query reports it REJECTED with nothing allocated).  Requests still
+ * running at the end keep their resources; dc_query's n_decisions counts the
+ * pod decisions of all attempts.  Blocking. */
+int dc_simulate(dc_t* dc, int32_t n_steps, const int32_t* submit_step, const int32_t* duration,
+                int32_t* start_step);
+
 /* --- general data-center graphs (Sec. V-D) ----------------------------------
  * The widest shortest path between two servers on an arbitrary undirected
  * graph (the paper's modified Dijkstra, one search per (source, destination)

@@ -86,6 +86,8 @@ def lib():
         L.orc_utilities.restype = None
         L.orc_fragmentation.argtypes = [C.c_void_p, _i64p, _i64p, _f64p, _f64p]
         L.orc_fragmentation.restype = None
+        L.orc_simulate.argtypes = [C.c_void_p, C.c_int32, C.POINTER(_Request), _i32p, _i32p,
+                                   C.c_int32, C.POINTER(_Result), _i32p]
         L.orc_graph_create.argtypes = [C.c_int32, C.c_int32, _i32p, _i32p, _i32p,
                                        C.POINTER(C.c_void_p)]
         L.orc_graph_destroy.argtypes = [C.c_void_p]
@@ -192,6 +194,33 @@ class OracleDC:
         a = np.ascontiguousarray(a, np.int32)
         if lib().orc_set_state(self.h, field, _p(a, _i32p), len(a)) != 0:
             raise ValueError("bad field")
+
+    def simulate(self, reqs, submit, duration, n_steps: int):
+        """Discrete-event simulation with queueing over the requests (orc_simulate):
+        returns (results, start steps)."""
+        keep = [_Req(q) for q in reqs]
+        n = len(keep)
+        arr = (_Request * max(1, n))(*[k.s for k in keep])
+        outs, res = [], (_Result * max(1, n))()
+        for i, k in enumerate(keep):
+            nc, m, P = len(k.a["pod"]), len(k.a["src"]), k.n_pods
+            o = {"host": np.zeros(nc, np.int32), "cpu": np.zeros(nc, np.int32),
+                 "mem": np.zeros(nc, np.int32), "bw": np.zeros(m, np.int32),
+                 "path": np.zeros(6 * m, np.int32), "pod_score": np.zeros(P, np.float64)}
+            outs.append(o)
+            res[i] = _Result(0, 0, *(_p(o[x], _i32p) for x in ("host", "cpu", "mem", "bw", "path")),
+                             _p(o["pod_score"], _f64p))
+        sub = np.ascontiguousarray(submit, np.int32)
+        dur = np.ascontiguousarray(duration, np.int32)
+        start = np.zeros(max(1, n), np.int32)
+        rc = lib().orc_simulate(self.h, n, arr, _p(sub, _i32p), _p(dur, _i32p), int(n_steps), res,
+                                _p(start, _i32p))
+        if rc != 0:
+            raise ValueError("orc_simulate failed: %d" % rc)
+        for i, o in enumerate(outs):
+            o["status"] = int(res[i].status)
+            o["n_decisions"] = int(res[i].n_decisions)
+        return outs, start[:n]
 
     def fragmentation(self):
         """(active servers, active links, F(N^s), F(E^s)) of the current state."""

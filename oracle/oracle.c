@@ -1060,3 +1060,80 @@ int32_t orc_graph_widest_path(const orc_graph* g, int32_t s, int32_t t, int32_t*
   free(ds); free(ws); free(dt); free(wt); free(queue);
   return D;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Discrete-event simulation with queueing (see oracle.h for the reading). */
+static const int32_t* g_sim_submit; /* qsort has no context argument */
+static int cmp_submit(const void* a, const void* b) {
+  const int32_t x = *(const int32_t*)a, y = *(const int32_t*)b;
+  if (g_sim_submit[x] != g_sim_submit[y]) return g_sim_submit[x] < g_sim_submit[y] ? -1 : 1;
+  return x < y ? -1 : (x > y ? 1 : 0);
+}
+
+int orc_simulate(orc_dc* d, int32_t n, const orc_request* reqs, const int32_t* submit,
+                 const int32_t* duration, int32_t T, orc_result* res, int32_t* start) {
+  if (n < 0 || T < 0) return ORC_EINVAL;
+  for (int32_t i = 0; i < n; ++i)
+    if (duration[i] < 1 || submit[i] < 0) return ORC_EINVAL;
+  int32_t* order = (int32_t*)malloc(sizeof(int32_t) * (n > 0 ? n : 1));
+  int32_t* end = (int32_t*)malloc(sizeof(int32_t) * (n > 0 ? n : 1));
+  for (int32_t i = 0; i < n; ++i) {
+    order[i] = i;
+    start[i] = -1;
+    end[i] = -1;
+    /* a request that is never tried: rejected, nothing allocated */
+    int32_t P = 0;
+    if (validate_request(&reqs[i], &P) != ORC_OK) {
+      free(order);
+      free(end);
+      return ORC_EINVAL;
+    }
+    res[i].status = ORC_REJECTED;
+    res[i].n_decisions = 0;
+    for (int32_t c = 0; c < reqs[i].n_containers; ++c) {
+      res[i].host[c] = -1;
+      res[i].cpu[c] = 0;
+      res[i].mem[c] = 0;
+    }
+    for (int32_t e = 0; e < reqs[i].n_edges; ++e) {
+      res[i].bw[e] = 0;
+      for (int j = 0; j < 6; ++j) res[i].path[(int64_t)e * 6 + j] = -1;
+    }
+    for (int32_t g = 0; g < P; ++g) res[i].pod_score[g] = -1.0;
+  }
+  g_sim_submit = submit;
+  qsort(order, (size_t)n, sizeof(int32_t), cmp_submit);
+  int32_t head = 0, arrived = 0, last_failed = -1;
+  int changed = 1;
+  int rc = ORC_OK;
+  for (int32_t t = 0; t < T && rc == ORC_OK; ++t) {
+    for (int32_t i = 0; i < n; ++i) /* departures */
+      if (end[i] == t) {
+        orc_release(d, &reqs[i], &res[i]);
+        end[i] = -1;
+        changed = 1;
+      }
+    while (arrived < n && submit[order[arrived]] <= t) ++arrived;
+    while (head < arrived) {
+      const int32_t r = order[head];
+      if (!changed && r == last_failed) break;
+      const int32_t prev = res[r].n_decisions;
+      rc = orc_schedule(d, &reqs[r], &res[r]);
+      if (rc != ORC_OK) break;
+      res[r].n_decisions += prev; /* decisions of every attempt */
+      if (res[r].status == ORC_ACCEPTED) {
+        start[r] = t;
+        end[r] = t + duration[r];
+        ++head;
+        changed = 1;
+      } else {
+        last_failed = r;
+        changed = 0;
+        break;
+      }
+    }
+  }
+  free(order);
+  free(end);
+  return rc;
+}

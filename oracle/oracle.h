@@ -126,6 +126,20 @@ void orc_utilities(const orc_request* req, const orc_result* res, double* u_cont
  * be NULL. */
 void orc_fragmentation(const orc_dc* dc, int64_t* active_servers, int64_t* active_links,
                        double* f_servers, double* f_links);
+/* Discrete-event simulation with queueing [Sec. IV-B.2, VI-A: requests carry
+ * a submission step and a running time counted in steps ("events"); a
+ * request that cannot be placed waits].  Reading: steps t = 0..n_steps-1; at
+ * each step (1) the requests whose running time ends at t leave (their
+ * resources return), (2) the requests submitted at t join the tail of one
+ * FCFS queue (submission step, then index), (3) the queue's head is
+ * scheduled, again and again: a placed request starts at t and leaves at
+ * t + duration; the first head that cannot be placed stays at the head, with
+ * every request behind it, and is tried again only in a later step in which
+ * something left (a failed attempt on an unchanged state would fail again).
+ * Requests that never start end REJECTED with start step -1.  results[i] and
+ * start[i] belong to reqs[i]; durations >= 1. */
+int orc_simulate(orc_dc* dc, int32_t n, const orc_request* reqs, const int32_t* submit,
+                 const int32_t* duration, int32_t n_steps, orc_result* results, int32_t* start);
 /* Widest shortest paths on a general undirected graph [Sec. V-D: the modified
  * Dijkstra that finds, between two servers, the shortest path with the most
  * available bandwidth; its links are stored once, u < v].  Links l = 0..L-1

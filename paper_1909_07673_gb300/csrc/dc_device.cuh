@@ -1931,12 +1931,88 @@ static __device__ void schedule_request(const Sm& s, const InstDev& I, int r) {
   __syncthreads();
   if (tid == 0 && writer) {
     I.o_status[r] = accepted ? DC_ACCEPTED : DC_REJECTED;
-    I.o_ndec[r] = c.ndec;
+    // a simulation retries requests: their decisions accumulate
+    I.o_ndec[r] = (I.sim_steps > 0 ? I.o_ndec[r] : 0) + c.ndec;
     I.o_tdone[r] = (long long)globaltimer_ns();
     atomicAdd(&I.counters[0], (unsigned long long)c.ndec);
     atomicAdd(&I.counters[1], (unsigned long long)c.ndec * (unsigned long long)c.H);
   }
   __syncthreads();
+}
+
+// Discrete-event simulation with queueing (Sec. IV-B.2, VI-A), the whole
+// run in one launch: steps t = 0..T-1; at each step the requests whose
+// running time ends leave (their resources return), the requests submitted
+// at t join the FCFS queue, and the queue's head is scheduled again and again;
+// a placed request starts at t and leaves at t + duration, the first head that
+// cannot be placed blocks the queue and is tried again only after something
+// left (a failed attempt on an unchanged state would fail again).  Requests
+// that never start end REJECTED with cleared outputs.  Every value that steers
+// the loop is read by all threads (and blocks) after a barrier.
+template <int B, int HPT, bool CL>
+static __device__ void simulate(const Sm& s, const InstDev& I) {
+  const int n = I.sim_n, T = I.sim_steps, tid = threadIdx.x;
+  const bool writer = s.c->rank == 0;
+  int head = 0, arrived = 0, last_failed = -1;
+  bool changed = true;
+  for (int t = 0; t < T; ++t) {
+    // the lists and statuses that steer the loop are written by thread 0 of
+    // block 0: read them from L2, so that every thread of every block takes
+    // the same path
+    for (int j = __ldcg(&I.sim_head[t]); j >= 0; j = __ldcg(&I.sim_next[j])) {
+      const int r = I.sim_req[j];
+      const ReqRec q = I.reqs[r];
+      give_back<B, CL>(s, I, q.c_off, q.n_c, q.e_off, q.n_e, false);  // ends with barriers
+      if (tid == 0 && writer) I.o_status[r] |= kReleased;
+      changed = true;
+    }
+    while (arrived < n && I.sim_submit[arrived] <= t) ++arrived;
+    while (head < arrived) {
+      if (!changed && head == last_failed) break;
+      const int r = I.sim_req[head];
+      schedule_request<B, HPT, CL>(s, I, r);  // ends with a barrier
+      if (CL) cl_sync();
+      const bool ok = (__ldcg(&I.o_status[r]) & 0xff) == DC_ACCEPTED;
+      if (ok && tid == 0 && writer) {
+        I.sim_start[head] = t;
+        const int e = t + I.sim_dur[head];
+        if (e < T) {
+          I.sim_next[head] = I.sim_head[e];
+          I.sim_head[e] = head;
+        }
+      }
+      __syncthreads();
+      if (CL) cl_sync();
+      if (!ok) {
+        last_failed = head;
+        changed = false;
+        break;
+      }
+      ++head;
+      changed = true;
+    }
+  }
+  // requests that were never tried: rejected, nothing allocated (the blocked
+  // head keeps what its last attempt left, as after any rejection)
+  if (writer)
+    for (int j = head; j < n; ++j) {
+      if (j == last_failed) continue;
+      const int r = I.sim_req[j];
+      const ReqRec q = I.reqs[r];
+      for (int i = tid; i < q.n_c; i += B) {
+        I.o_host[q.c_off + i] = -1;
+        I.o_cpu[q.c_off + i] = 0;
+        I.o_mem[q.c_off + i] = 0;
+      }
+      for (int e = tid; e < q.n_e; e += B) {
+        I.o_bw[q.e_off + e] = 0;
+        for (int k = 0; k < 6; ++k) I.o_path[(q.e_off + e) * 6 + k] = -1;
+      }
+      for (int p = tid; p < q.n_p; p += B) I.o_score[q.p_off + p] = -1.0;
+      if (tid == 0) I.o_status[r] = DC_REJECTED;
+    }
+  __syncthreads();
+  if (CL) cl_sync();
 }
 
 // One data center per thread block (CL = false), or per thread-block cluster
@@ -1949,11 +2025,12 @@ __global__ void __launch_bounds__(B, 1) k_schedule(const InstDev* __restrict__ i
   if (threadIdx.x == 0) atomicMin(&I.counters[2], globaltimer_ns());
   load_instance<B, CL>(s, I);
   const bool writer = s.c->rank == 0;
-  for (int op = 0; op < I.n_ops; ++op) {
+  if (I.sim_steps > 0) simulate<B, HPT, CL>(s, I);
+  for (int op = 0; op < (I.sim_steps > 0 ? 0 : I.n_ops); ++op) {
     const int w = I.ops[op];
     const int r = w & (kOpRelease - 1);
     if (w & kOpRelease) {
-      const int st = I.o_status[r];
+      const int st = __ldcg(&I.o_status[r]);  // from L2: the same value in every block
       if ((st & 0xff) == DC_ACCEPTED && !(st & kReleased)) {
         const ReqRec q = I.reqs[r];
         give_back<B, CL>(s, I, q.c_off, q.n_c, q.e_off, q.n_e, false);

@@ -98,6 +98,14 @@ struct InstDev {
   // blocks sharing this data center (a thread-block cluster when > 1; the
   // state is then global and k is a multiple of ncta)
   int32_t ncta;
+  // discrete-event simulation with queueing (sim_steps > 0; ops unused):
+  // sim_n requests in FCFS order (sim_req: request index, sim_submit:
+  // submission step, non-decreasing; sim_dur: running time); outputs
+  // sim_start (-1 = never started); scratch sim_head [sim_steps] (-1) and
+  // sim_next [sim_n]: per step, the list of requests that leave then
+  int32_t sim_steps, sim_n;
+  const int32_t *sim_req, *sim_submit, *sim_dur;
+  int32_t *sim_start, *sim_head, *sim_next;
   int4* scr_pe;       // peer links of the pod being placed
   PodLog* scr_log;    // [pods of the current request]
   // AHP DIFF scratch, [H] each (null for the other methods): viable host

@@ -787,6 +787,7 @@ struct PlanOpts {
   size_t max_ops = SIZE_MAX;
   const LaunchCfg* shapes = nullptr;
   bool claim = true;
+  const InstDev* sim = nullptr;  // simulation fields for a one-instance plan
 };
 
 int plan_create(dc_t* const* dcs, int32_t n, int32_t flags, const PlanOpts& opt, dc_plan** out) {
@@ -862,6 +863,18 @@ int plan_create(dc_t* const* dcs, int32_t n, int32_t flags, const PlanOpts& opt,
       p->h_desc.push_back(
           make_desc(d, p->d_ops + op_base[i], (int)(op1[i] - op0[i]), p->d_counters, &L));
       if (!opt.claim) p->h_desc.back().progress = nullptr;
+      if (opt.sim) {
+        InstDev& D = p->h_desc.back();
+        D.sim_steps = opt.sim->sim_steps;
+        D.sim_n = opt.sim->sim_n;
+        D.sim_req = opt.sim->sim_req;
+        D.sim_submit = opt.sim->sim_submit;
+        D.sim_dur = opt.sim->sim_dur;
+        D.sim_start = opt.sim->sim_start;
+        D.sim_head = opt.sim->sim_head;
+        D.sim_next = opt.sim->sim_next;
+        D.progress = nullptr;
+      }
       p->inst_of.push_back(i);
       bool same = !p->groups.empty();
       if (same) {
@@ -981,6 +994,74 @@ bool same_shape(const LaunchCfg& a, const LaunchCfg& b) {
 }  // namespace
 
 extern "C" {
+
+int dc_simulate(dc_t* d, int32_t n_steps, const int32_t* submit_step, const int32_t* duration,
+                int32_t* start_step) {
+  if (!d || n_steps < 1) return DC_E_INVAL;
+  settle(d, true);
+  const size_t o0 = d->ops_claimed, o1 = d->ops.size();
+  const int32_t n = (int32_t)(o1 - o0);
+  if (n == 0) return DC_OK;
+  if (!submit_step || !duration || !start_step) return DC_E_INVAL;
+  for (size_t o = o0; o < o1; ++o)
+    if (d->ops[o] & kOpRelease) return DC_E_BUSY;  // only submissions can be simulated
+  for (int32_t i = 0; i < n; ++i)
+    if (submit_step[i] < 0 || duration[i] < 1) return DC_E_INVAL;
+  // FCFS order: submission step, then submission order
+  std::vector<int32_t> order(n);
+  for (int32_t i = 0; i < n; ++i) order[i] = i;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int32_t a, int32_t b) { return submit_step[a] < submit_step[b]; });
+  std::vector<int32_t> h_req(n), h_sub(n), h_dur(n);
+  for (int32_t j = 0; j < n; ++j) {
+    h_req[j] = d->ops[o0 + order[j]];
+    h_sub[j] = submit_step[order[j]];
+    h_dur[j] = duration[order[j]];
+  }
+  cudaStream_t st = d->stream;
+  int32_t* buf = nullptr;  // req, submit, dur, start, next [n] each, head [n_steps]
+  const size_t words = 5 * (size_t)n + std::max<size_t>(1, n_steps);
+  if (cudaMallocAsync((void**)&buf, words * 4, st) != cudaSuccess) return DC_E_NOMEM;
+  InstDev sim{};
+  sim.sim_steps = n_steps;
+  sim.sim_n = n;
+  sim.sim_req = buf;
+  sim.sim_submit = buf + n;
+  sim.sim_dur = buf + 2 * n;
+  sim.sim_start = buf + 3 * n;
+  sim.sim_next = buf + 4 * n;
+  sim.sim_head = buf + 5 * n;
+  int rc = cuda_rc(cudaMemcpyAsync(buf, h_req.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, st));
+  if (rc == DC_OK)
+    rc = cuda_rc(cudaMemcpyAsync(buf + n, h_sub.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, st));
+  if (rc == DC_OK)
+    rc = cuda_rc(cudaMemcpyAsync(buf + 2 * n, h_dur.data(), 4 * (size_t)n, cudaMemcpyHostToDevice, st));
+  if (rc == DC_OK)
+    rc = cuda_rc(cudaMemsetAsync(buf + 3 * n, 0xff, 4 * ((size_t)2 * n + std::max(1, n_steps)), st));
+  dc_plan* p = nullptr;
+  if (rc == DC_OK) {
+    PlanOpts o;
+    o.sim = &sim;
+    dc_t* one[1] = {d};
+    rc = plan_create(one, 1, 0, o, &p);
+  }
+  // decisions accumulate over a request's attempts
+  if (rc == DC_OK) {
+    rc = cuda_rc(cudaMemsetAsync(d->o_ndec.p + p->req_begin[0], 0,
+                                 4 * (p->req_end[0] - p->req_begin[0]), p->home));
+  }
+  if (rc == DC_OK) rc = dc_plan_launch(p, p->home);
+  if (rc == DC_OK) rc = dc_plan_collect(p);
+  std::vector<int32_t> h_start(n);
+  if (rc == DC_OK)
+    rc = cuda_rc(cudaMemcpy(h_start.data(), buf + 3 * n, 4 * (size_t)n, cudaMemcpyDeviceToHost));
+  if (rc == DC_OK)
+    for (int32_t j = 0; j < n; ++j) start_step[order[j]] = h_start[j];
+  if (p) dc_plan_destroy(p);
+  cudaFreeAsync(buf, st);
+  const int rc2 = cuda_rc(cudaStreamSynchronize(st));
+  return rc != DC_OK ? rc : rc2;
+}
 
 int dc_autotune(dc_t* const* dcs, int32_t n, int32_t max_ops, dc_tune_entry* out,
                 int32_t max_out, int32_t* n_out) {

@@ -109,6 +109,7 @@ def lib():
         L.dc_plan_stats.argtypes = [C.c_void_p, _i64p, _i64p, _i32p, _i64p]
         L.dc_plan_destroy.argtypes = [C.c_void_p]
         L.dc_plan_destroy.restype = None
+        L.dc_simulate.argtypes = [C.c_void_p, C.c_int32, _i32p, _i32p, _i32p]
         L.dc_utilities.argtypes = [C.c_void_p, C.c_int64, _f64p, _f64p]
         L.dc_utility_summary.argtypes = [C.c_void_p, _f64p, _i64p, _f64p, _i64p]
         L.dc_fragmentation.argtypes = [C.c_void_p, _i64p, _i64p, _f64p, _f64p]
@@ -229,6 +230,16 @@ class DataCenter:
         _check(lib().dc_submit_batch(self.h, len(reqs), arr, _p(ids, _i64p)), "dc_submit_batch")
         self._reqs.extend(reqs)
         return int(ids[0])
+
+    def simulate(self, n_steps: int, submit_step, duration) -> np.ndarray:
+        """Discrete-event simulation of the queued requests (dc_simulate);
+        returns each one's start step (-1: never started)."""
+        sub = np.ascontiguousarray(submit_step, np.int32)
+        dur = np.ascontiguousarray(duration, np.int32)
+        start = np.zeros(max(1, len(sub)), np.int32)
+        _check(lib().dc_simulate(self.h, int(n_steps), _p(sub, _i32p), _p(dur, _i32p),
+                                 _p(start, _i32p)), "dc_simulate")
+        return start[:len(sub)]
 
     def utilities(self, req_id: int):
         """(U(i) per container, U(ij) per link) of a scheduled request

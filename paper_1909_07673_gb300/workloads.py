@@ -402,6 +402,36 @@ def serving(seed: int = 3, method: int = TOPSIS, pair_rule: int = RATIO, scheme:
     return Workload("serving", insts, np.asarray(times), inst_of.astype(np.int64), local)
 
 
+def simulation(seed: int = 5, method: int = TOPSIS, pair_rule: int = RATIO,
+               scheme: str = "flat", k: int = 20, n_requests: int = 6000, n_steps: int = 500,
+               max_duration: int = 250, host_cpu: int = 24, host_mem: int = 256,
+               link_mbps: int = 1000, n_criteria: int = 6):
+    """The discrete-event scenario of the paper's GPU evaluation: an empty
+    k-port fat-tree of host_cpu-core / host_mem-GB hosts and link_mbps links;
+    n_requests of 4 containers (CPU U{1..2}, memory U{1..4}), up to half of a
+    request's containers grouped in one pod, an Erdos-Renyi p=0.5 graph made
+    connected with U{1..50} Mbps per link; submission step U{0..n_steps-1}
+    and running time U{1..max_duration}.  Returns (workload, submit,
+    duration)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    reqs = []
+    for _ in range(n_requests):
+        q = gen_request(rng, 4, p_edge=0.5, bw=lambda r, m: r.integers(1, 51, m), cpu_hi=2,
+                        mem_hi=4)
+        g = int(rng.integers(0, 3))  # containers grouped in pod 0 (0-2 of 4)
+        if g >= 2:
+            pod = np.concatenate([[0] * g, np.arange(1, 4 - g + 1)]).astype(np.int32)
+            q["pod"] = pod
+            # links inside the pod stay; pod ids are dense and ordered
+        reqs.append(q)
+    submit = np.sort(rng.integers(0, n_steps, n_requests)).astype(np.int32)
+    duration = rng.integers(1, max_duration + 1, n_requests).astype(np.int32)
+    W6 = WEIGHTS[n_criteria][scheme]
+    inst = Instance(k, host_cpu, host_mem, link_mbps, n_criteria, method, pair_rule, W6,
+                    None, None, None, pack_requests(reqs))
+    return Workload("simulation", [inst]), submit, duration
+
+
 def serving_events(wl: Workload):
     """Flattens a serving workload into one timed event list: each arrival
     (time, instance, kind 0, request index within the instance) followed by the
