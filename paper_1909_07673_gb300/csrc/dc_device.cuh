@@ -98,6 +98,7 @@ struct Ctx {
   int32_t size, npe;
   int32_t need1, need1h, need2;
   int32_t hash_ok;
+  int32_t nhash;      // hash slots in use (listed in s.hused)
   int32_t nfail;
   // commit prefilter (exact necessary condition, see commit_possible)
   long long bw_total;  // sum of bw_min over the pod's links to placed containers
@@ -144,6 +145,7 @@ struct Sm {
   uint32_t* tmark;    // [B] bit j of word t: host t + j*B hosts a neighbour
   uint32_t* trymask;  // [B] bit j of word t: host t + j*B failed a commit
   int32_t *hkey, *hcnt;  // [kHash]
+  int32_t* hused;        // [kHash] slots taken by the current pod (c.nhash of them)
   long long* hsum;       // [kHash] sum of bw_min of the links to that host
   long long* red64;
   int32_t* red32;
@@ -179,6 +181,7 @@ static __device__ __forceinline__ Sm carve(unsigned char* base, const InstDev& I
   s.trymask = reinterpret_cast<uint32_t*>(base + L.trymask);
   s.hkey = reinterpret_cast<int32_t*>(base + L.hkey);
   s.hcnt = reinterpret_cast<int32_t*>(base + L.hcnt);
+  s.hused = reinterpret_cast<int32_t*>(base + L.hused);
   s.hsum = reinterpret_cast<long long*>(base + L.hsum);
   s.red64 = reinterpret_cast<long long*>(base + L.red64);
   s.red32 = reinterpret_cast<int32_t*>(base + L.red32);
@@ -516,6 +519,7 @@ static __device__ void pod_setup_warp(const Sm& s, const InstDev& I, int g, Pre&
       bool ins = false;
       for (int p = 0; p < kHash / 2; ++p) {  // bounded probing
         const int old = atomicCAS(&s.hkey[h], -1, hv);
+        if (old == -1) s.hused[atomicAdd(&c.nhash, 1)] = (int)h;
         if (old == -1 || old == hv) {
           atomicAdd(&s.hcnt[h], 1);
           atomicAdd((unsigned long long*)&s.hsum[h], (unsigned long long)q.z);
@@ -539,17 +543,16 @@ static __device__ void pod_setup_warp(const Sm& s, const InstDev& I, int g, Pre&
   // neighbour hosts whose own uplink cannot carry the pod's links to them
   long long tot = 0;
   int n_over = 0, h_over = -1;
-  if (npe > 0)
-    for (int h = lane; h < kHash; h += 32) {
-      const int key = s.hkey[h];
-      if (key >= 0) {
-        tot += s.hsum[h];
-        if (s.hsum[h] > (long long)s.lk[key]) {
-          ++n_over;
-          h_over = key;
-        }
-      }
+  const int nhash = c.nhash;
+  for (int i = lane; i < nhash; i += 32) {
+    const int h = s.hused[i];
+    const int key = s.hkey[h];
+    tot += s.hsum[h];
+    if (s.hsum[h] > (long long)s.lk[key]) {
+      ++n_over;
+      h_over = key;
     }
+  }
   for (int o = 16; o > 0; o >>= 1) {
     tot += __shfl_xor_sync(0xffffffffu, tot, o);
     n_over += __shfl_xor_sync(0xffffffffu, n_over, o);
@@ -578,7 +581,7 @@ static __device__ void pod_setup_warp(const Sm& s, const InstDev& I, int g, Pre&
 // Undoes the pod's neighbour bookkeeping (warp 0, end of a pod).
 template <int B>
 static __device__ void pod_clear_warp(const Sm& s) {
-  const Ctx& c = *s.c;
+  Ctx& c = *s.c;
   const int lane = lane_id();
   for (int i = lane; i < c.npe; i += 32) {
     const int hv = c.pel[i].y;
@@ -587,12 +590,14 @@ static __device__ void pod_clear_warp(const Sm& s) {
     s.Cp[div_half(c, ev)] = 0;
     s.tmark[hv % B] = 0u;
   }
-  if (c.npe > 0)
-    for (int h = lane; h < kHash; h += 32) {
-      s.hkey[h] = -1;
-      s.hcnt[h] = 0;
-      s.hsum[h] = 0;
-    }
+  for (int i = lane; i < c.nhash; i += 32) {
+    const int h = s.hused[i];
+    s.hkey[h] = -1;
+    s.hcnt[h] = 0;
+    s.hsum[h] = 0;
+  }
+  __syncwarp();
+  if (lane == 0) c.nhash = 0;
   if (c.nfail > 0)
     for (int t = lane; t < B; t += 32) s.trymask[t] = 0u;
 }
@@ -1559,17 +1564,20 @@ static __device__ bool commit_reserve(const Sm& s, const InstDev& I, int g) {
   // decision record for the FP64 score: the criteria of u before any of
   // this pod's reservations, as selected (rewritten by a later attempt if
   // this one fails)
-  if (tid == 0) {
+  {
     PodLog* L = I.scr_log + g;
-    for (int v = 0; v < kMaxC; ++v) {
+    if (tid < kMaxC) {  // one thread per criterion
+      const int v = tid;
       L->x[v] = v < c.C ? c.xw[v] : 0;
       L->mx[v] = c.mx[v];
       L->mn[v] = c.mn[v];
       L->S1[v] = c.S1[v];
       L->S2[v] = c.S2[v];
     }
-    L->n = c.n;
-    L->score = c.wscore;
+    if (tid == 0) {
+      L->n = c.n;
+      L->score = c.wscore;
+    }
   }
   if (BLK) __syncthreads(); else __syncwarp();
   int done = 0;  // peer links committed so far
@@ -1755,6 +1763,7 @@ static __device__ void load_instance(const Sm& s, const InstDev& I) {
     s.hcnt[h] = 0;
     s.hsum[h] = 0;
   }
+  if (tid == 0) c.nhash = 0;
   s.tmark[tid] = 0;
   s.trymask[tid] = 0;
   __syncthreads();
