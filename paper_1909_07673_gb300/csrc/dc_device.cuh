@@ -93,6 +93,13 @@ struct Ctx {
   const int32_t* pe;  // pod -> link range
   int32_t* hof;       // container -> host (shared copy, or the global output)
   int4* pel;          // peer links of the current pod (shared, or global scratch)
+  int4* curc;         // [32] container records of the current pod (shared)
+  // the pod set up ahead while the current one commits: its peer links,
+  // container records and the fields the commit reads
+  int4 *pel_n, *curc_n;
+  int32_t npe_n, size_n;
+  long long dmax_cpu_n, dmax_mem_n;
+  int32_t pel_smem;   // peer links in shared memory (both copies)
   // pod
   long long dmin_cpu, dmax_cpu, dmin_mem, dmax_mem;
   int32_t size, npe;
@@ -151,8 +158,8 @@ struct Sm {
   int32_t* red32;
   unsigned char* sel;
   int32_t *st_pc, *st_pe, *st_hof;
-  int4* pel;
-  int4* curc;  // [32] container records of the pod being placed
+  int4 *pel, *pel2;    // [kPeS] two peer-link buffers
+  int4 *curc, *curc2;  // [32] two container-record buffers
   int32_t* xwarp;  // [B / 32][kMaxC + 1] criteria of each warp's leader, mixed flag
   int32_t *wg, *wm;  // [E] each: wide table passes (global-state data centers)
 };
@@ -191,6 +198,8 @@ static __device__ __forceinline__ Sm carve(unsigned char* base, const InstDev& I
   s.st_hof = reinterpret_cast<int32_t*>(base + L.st_hof);
   s.pel = reinterpret_cast<int4*>(base + L.pel);
   s.curc = reinterpret_cast<int4*>(base + L.curc);
+  s.pel2 = reinterpret_cast<int4*>(base + L.pel2);
+  s.curc2 = reinterpret_cast<int4*>(base + L.curc2);
   s.xwarp = reinterpret_cast<int32_t*>(base + L.xwarp);
   s.wg = reinterpret_cast<int32_t*>(base + L.wide);
   s.wm = s.wg + E;
@@ -470,18 +479,60 @@ static __device__ __forceinline__ Pre prefetch_pod(const Ctx& c, const InstDev& 
   return p;
 }
 
-// a1: pod demand and the pod's links to containers of earlier pods (warp 0).
-// `cur` holds the pod's prefetched records; on return `cur` holds those of
-// pod g + 1.
-template <int B>
-static __device__ void pod_setup_warp(const Sm& s, const InstDev& I, int g, Pre& cur) {
+// Neighbour hosts whose own uplink cannot carry the pod's links to them
+// (the commit prefilter), from the pod's hash of neighbour hosts and the
+// current link residuals (one warp).
+static __device__ void pod_uplink_check_warp(const Sm& s) {
   Ctx& c = *s.c;
   const int lane = lane_id();
+  long long tot = 0;
+  int n_over = 0, h_over = -1;
+  const int nhash = c.nhash;
+  for (int i = lane; i < nhash; i += 32) {
+    const int h = s.hused[i];
+    const int key = s.hkey[h];
+    tot += s.hsum[h];
+    if (s.hsum[h] > (long long)s.lk[key]) {
+      ++n_over;
+      h_over = key;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    n_over += __shfl_xor_sync(0xffffffffu, n_over, o);
+    h_over = imax(h_over, __shfl_xor_sync(0xffffffffu, h_over, o));
+  }
+  if (lane == 0) {
+    c.bw_total = tot;
+    c.n_over = n_over;
+    c.h_over = h_over;
+  }
+  __syncwarp();
+}
+
+// Set-up modes: the records of the pod come from the prefetch registers (or
+// from global memory); the set-up writes the current pod's fields (or, ahead
+// of a commit, the second copy of the fields the commit reads, and leaves the
+// uplink check and the failure count to after the commit).
+enum { kSetupAhead = 1, kSetupFromGlobal = 2 };
+
+// a1: pod demand and the pod's links to containers of earlier pods (one
+// warp).  `cur` holds the pod's prefetched records; on return `cur` holds
+// those of pod g + 1.
+template <int B>
+static __device__ void pod_setup_warp(const Sm& s, const InstDev& I, int g, Pre& cur,
+                                      int mode = 0) {
+  Ctx& c = *s.c;
+  const int lane = lane_id();
+  const bool ahead = mode & kSetupAhead;
+  const bool pre = !(mode & kSetupFromGlobal);
+  int4* curc = ahead ? c.curc_n : c.curc;
+  int4* pel = ahead ? c.pel_n : c.pel;
   const int32_t c0 = c.pc[g], c1 = c.pc[g + 1];
   long long dmin_c = 0, dmax_c = 0, dmin_m = 0, dmax_m = 0;
   for (int pos = c0 + lane; pos < c1; pos += 32) {
-    const int4 q = pos - c0 < 32 ? cur.c : I.c_lay[c.c_off + pos];
-    if (pos - c0 < 32) s.curc[lane] = q;
+    const int4 q = (pre && pos - c0 < 32) ? cur.c : I.c_lay[c.c_off + pos];
+    if (pos - c0 < 32) curc[lane] = q;
     dmin_c += q.y & 0xffff;
     dmax_c += (unsigned)q.y >> 16;
     dmin_m += q.z & 0xffff;
@@ -503,14 +554,14 @@ static __device__ void pod_setup_warp(const Sm& s, const InstDev& I, int g, Pre&
     int4 q = make_int4(0, 0, 0, 0);
     int hv = 0;
     if (pos < e1) {
-      q = base == e0 ? cur.e : I.e_lay[c.e_off + pos];
+      q = (pre && base == e0) ? cur.e : I.e_lay[c.e_off + pos];
       peer = !(q.x & kLinkIntra);
       if (peer) hv = c.hof[q.y];
     }
     const unsigned m = __ballot_sync(0xffffffffu, peer);
     if (peer) {
       const int slot = npe + __popc(m & ((1u << lane) - 1u));
-      c.pel[slot] = make_int4(q.x, hv, q.z, q.w);
+      pel[slot] = make_int4(q.x, hv, q.z, q.w);
       const int ev = div_half(c, hv);
       atomicAdd(&s.Be[ev], 1);
       atomicAdd(&s.Cp[div_half(c, ev)], 1);
@@ -540,51 +591,42 @@ static __device__ void pod_setup_warp(const Sm& s, const InstDev& I, int g, Pre&
   }
   hash_ok = __all_sync(0xffffffffu, hash_ok);
   __syncwarp();
-  // neighbour hosts whose own uplink cannot carry the pod's links to them
-  long long tot = 0;
-  int n_over = 0, h_over = -1;
-  const int nhash = c.nhash;
-  for (int i = lane; i < nhash; i += 32) {
-    const int h = s.hused[i];
-    const int key = s.hkey[h];
-    tot += s.hsum[h];
-    if (s.hsum[h] > (long long)s.lk[key]) {
-      ++n_over;
-      h_over = key;
-    }
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    tot += __shfl_xor_sync(0xffffffffu, tot, o);
-    n_over += __shfl_xor_sync(0xffffffffu, n_over, o);
-    h_over = imax(h_over, __shfl_xor_sync(0xffffffffu, h_over, o));
-  }
   if (lane == 0) {
     c.dmin_cpu = dmin_c;
-    c.dmax_cpu = dmax_c;
     c.dmin_mem = dmin_m;
-    c.dmax_mem = dmax_m;
-    c.size = c1 - c0;
-    c.npe = npe;
     c.need1 = nd.v1;
     c.need1h = nd.h1;
     c.need2 = nd.v2;
     c.hash_ok = hash_ok ? 1 : 0;
-    c.nfail = 0;
-    c.bw_total = tot;
-    c.n_over = n_over;
-    c.h_over = h_over;
+    if (ahead) {
+      c.dmax_cpu_n = dmax_c;
+      c.dmax_mem_n = dmax_m;
+      c.size_n = c1 - c0;
+      c.npe_n = npe;
+    } else {
+      c.dmax_cpu = dmax_c;
+      c.dmax_mem = dmax_m;
+      c.size = c1 - c0;
+      c.npe = npe;
+      if (!(mode & kSetupFromGlobal)) c.nfail = 0;
+    }
   }
+  __syncwarp();
+  if (!ahead) pod_uplink_check_warp(s);
   cur = prefetch_pod(c, I, g + 1);
   __syncwarp();
 }
 
-// Undoes the pod's neighbour bookkeeping (warp 0, end of a pod).
+// Undoes the pod's neighbour bookkeeping (one warp, end of a pod); `ahead`:
+// that of the pod set up ahead; the failed-host mask only with `trymask`.
 template <int B>
-static __device__ void pod_clear_warp(const Sm& s) {
+static __device__ void pod_clear_warp(const Sm& s, bool ahead = false, bool trymask = true) {
   Ctx& c = *s.c;
   const int lane = lane_id();
-  for (int i = lane; i < c.npe; i += 32) {
-    const int hv = c.pel[i].y;
+  const int npe = ahead ? c.npe_n : c.npe;
+  const int4* pel = ahead ? c.pel_n : c.pel;
+  for (int i = lane; i < npe; i += 32) {
+    const int hv = pel[i].y;
     const int ev = div_half(c, hv);
     s.Be[ev] = 0;
     s.Cp[div_half(c, ev)] = 0;
@@ -598,7 +640,7 @@ static __device__ void pod_clear_warp(const Sm& s) {
   }
   __syncwarp();
   if (lane == 0) c.nhash = 0;
-  if (c.nfail > 0)
+  if (trymask && c.nfail > 0)
     for (int t = lane; t < B; t += 32) s.trymask[t] = 0u;
 }
 
@@ -1531,7 +1573,7 @@ static __device__ void commit_capacity(const Sm& s, const InstDev& I, int g) {
   const int32_t c0 = c.pc[g], c1 = c.pc[g + 1];
   uint32_t used_c = 0, used_m = 0;
   for (int pos = c0 + lane; pos < c1; pos += 32) {
-    const int4 q = pos - c0 < 32 ? s.curc[lane] : I.c_lay[c.c_off + pos];
+    const int4 q = pos - c0 < 32 ? c.curc[lane] : I.c_lay[c.c_off + pos];
     const int a = take_cpu_max ? ((unsigned)q.y >> 16) : (q.y & 0xffff);
     const int m = take_mem_max ? ((unsigned)q.z >> 16) : (q.z & 0xffff);
     I.o_host[c.c_off + q.x] = u;
@@ -1664,7 +1706,7 @@ static __device__ void commit_finish(const Sm& s, const InstDev& I, int g, Pre& 
   if (c.hof_smem || c.rank == 0) {
     const int32_t c0 = c.pc[g], c1 = c.pc[g + 1];
     for (int pos = c0 + lane; pos < c1; pos += 32) {
-      const int4 q = pos - c0 < 32 ? s.curc[lane] : I.c_lay[c.c_off + pos];
+      const int4 q = pos - c0 < 32 ? c.curc[lane] : I.c_lay[c.c_off + pos];
       c.hof[q.x] = u;
     }
   }
@@ -1802,6 +1844,10 @@ static __device__ void load_request(const Sm& s, const InstDev& I, int r, const 
     c.hof_smem = stage_c ? 1 : 0;
     // blocks of a cluster each have their own peer-link scratch
     c.pel = q.max_pe <= kPeS ? s.pel : I.scr_pe + (int64_t)c.rank * I.scr_links;
+    c.pel_n = s.pel2;
+    c.pel_smem = q.max_pe <= kPeS ? 1 : 0;
+    c.curc = s.curc;
+    c.curc_n = s.curc2;
     c.npe = 0;
     c.nfail = 0;
     c.ndec = 0;
@@ -1816,8 +1862,85 @@ static __device__ void load_request(const Sm& s, const InstDev& I, int r, const 
   __syncthreads();
 }
 
-// One pod decision (a2..a8); pod g was set up by warp 0 before.  Returns
-// true when the pod is placed (then pod g + 1 is set up).  In a cluster,
+// The hosts of pod g's containers in the request's host map (as its commit
+// sets them: u, or -1 to undo).  One warp.
+static __device__ void set_pod_hosts(const Sm& s, const InstDev& I, int g, int u) {
+  Ctx& c = *s.c;
+  const int lane = lane_id();
+  const int32_t c0 = c.pc[g], c1 = c.pc[g + 1];
+  for (int pos = c0 + lane; pos < c1; pos += 32) {
+    const int4 q = pos - c0 < 32 ? c.curc[lane] : I.c_lay[c.c_off + pos];
+    c.hof[q.x] = u;
+  }
+  __syncwarp();
+}
+
+// Warp 1 of the one-block shared-memory kernel, while warp 0 commits pod g on
+// the chosen host: ends pod g's neighbour bookkeeping and sets up pod g + 1
+// as if the commit succeeds (the host map, the tables and hashes of the pod
+// are not read by the commit; the fields it reads get the second copy).
+template <int B>
+static __device__ void setup_ahead_warp(const Sm& s, const InstDev& I, int g, Pre& nxt) {
+  set_pod_hosts(s, I, g, s.c->winner);
+  pod_clear_warp<B>(s, false, false);  // the failed-host mask stays until the outcome
+  __syncwarp();
+  pod_setup_warp<B>(s, I, g + 1, nxt, kSetupAhead);
+}
+
+// Warp 1 after the commit of pod g.  Success: the pod set up ahead becomes
+// the current one (its uplink check runs on the state after the commit), or,
+// without a set-up ahead, pod g ends and pod g + 1 is set up now.  Failure:
+// the host is masked and, after a set-up ahead, pod g's bookkeeping is built
+// again (its failure count kept) for the next pick.
+template <int B>
+static __device__ void after_commit_warp(const Sm& s, const InstDev& I, int g, Pre& nxt,
+                                         bool ahead) {
+  Ctx& c = *s.c;
+  const int lane = lane_id();
+  const int u = c.winner;
+  if (c.commit_ok) {
+    if (ahead) {
+      if (c.nfail > 0)
+        for (int t = lane; t < B; t += 32) s.trymask[t] = 0u;
+      __syncwarp();
+      if (lane == 0) {
+        int4* t = c.pel;
+        c.pel = c.pel_n;
+        c.pel_n = t;
+        t = c.curc;
+        c.curc = c.curc_n;
+        c.curc_n = t;
+        c.npe = c.npe_n;
+        c.size = c.size_n;
+        c.dmax_cpu = c.dmax_cpu_n;
+        c.dmax_mem = c.dmax_mem_n;
+        c.nfail = 0;
+      }
+      __syncwarp();
+      pod_uplink_check_warp(s);
+    } else {
+      set_pod_hosts(s, I, g, u);
+      pod_clear_warp<B>(s);
+      __syncwarp();
+      if (g + 1 < c.n_p) pod_setup_warp<B>(s, I, g + 1, nxt);
+    }
+    return;
+  }
+  if (lane == 0) {
+    atomicOr(&s.trymask[u % B], 1u << (u / B));
+    c.nfail += 1;
+  }
+  __syncwarp();
+  if (ahead) {
+    set_pod_hosts(s, I, g, -1);
+    pod_clear_warp<B>(s, true, false);
+    __syncwarp();
+    pod_setup_warp<B>(s, I, g, nxt, kSetupFromGlobal);
+  }
+}
+
+// One pod decision (a2..a8); pod g was set up before.  Returns true when the
+// pod is placed (then pod g + 1 is set up).  In a cluster,
 // block 0 commits on the shared state and the others learn the result
 // after a cluster barrier.
 template <int B, int HPT, bool CL>
@@ -1849,9 +1972,18 @@ static __device__ bool decide_pod(const Sm& s, const InstDev& I, int g, Pre& nxt
     } else if (I.state_global) {
       const bool ok = commit_reserve<B, true>(s, I, g);
       if (tid < 32) commit_finish<B>(s, I, g, nxt, ok);
-    } else if (tid < 32) {
-      const bool ok = commit_reserve<B, false>(s, I, g);
-      commit_finish<B>(s, I, g, nxt, ok);
+    } else {
+      // one block, state in shared memory: warp 0 commits pod g while warp 1
+      // sets up pod g + 1 ahead; warp 1 then settles the outcome
+      const bool ahead = g + 1 < c.n_p && c.pel_smem && c.hof_smem;
+      if (tid < 32) {
+        const bool ok = commit_reserve<B, false>(s, I, g);
+        if (tid == 0) c.commit_ok = ok ? 1 : 0;
+      } else if (tid < 64 && ahead) {
+        setup_ahead_warp<B>(s, I, g, nxt);
+      }
+      __syncthreads();
+      if (tid >= 32 && tid < 64) after_commit_warp<B>(s, I, g, nxt, ahead);
     }
     __syncthreads();
     if (c.commit_ok) {
@@ -1917,7 +2049,11 @@ static __device__ void schedule_request(const Sm& s, const InstDev& I, int r) {
     for (int p = tid; p < n_p; p += B) I.o_score[p_off + p] = -1.0;
   }
   Pre nxt = {make_int4(0, 0, 0, 0), make_int4(0, 0, 0, 0)};
-  if (tid < 32 && n_p > 0) {
+  // the warp that sets up pods (and holds the prefetched records): warp 1 in
+  // the one-block shared-memory kernel (it sets up ahead of the commits),
+  // warp 0 otherwise
+  const int setup_warp = (!CL && !I.state_global) ? 1 : 0;
+  if ((tid >> 5) == setup_warp && n_p > 0) {
     nxt = prefetch_pod(c, I, 0);
     pod_setup_warp<B>(s, I, 0, nxt);
   }

@@ -130,7 +130,7 @@ DC_HD inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 // Shared-memory layout of one scheduling block (bytes), see dc_kernels.cu.
 struct SmemLayout {
   size_t ctx, cm, ctr, lk, tab, cp, tmark, trymask, hkey, hcnt, hused, hsum, red64, red32, sel;
-  size_t st_pc, st_pe, st_hof, pel, curc, xwarp, wide, total;
+  size_t st_pc, st_pe, st_hof, pel, curc, pel2, curc2, xwarp, wide, total;
 };
 
 // Link residuals in shared memory: host links [0, H), then edge-aggregation
@@ -168,6 +168,9 @@ DC_HD inline SmemLayout smem_layout(int k, int block, size_t ctx_bytes, bool sta
   L.st_hof = o; o = align_up(o + 4 * (size_t)kStageC, 16);
   L.pel = o; o = align_up(o + 16 * (size_t)kPeS, 16);
   L.curc = o; o = align_up(o + 16 * 32, 16);
+  // second copies for the pod set up ahead of a commit
+  L.pel2 = o; o = align_up(o + 16 * (size_t)kPeS, 16);
+  L.curc2 = o; o = align_up(o + 16 * 32, 16);
   L.xwarp = o; o = align_up(o + 4 * nw * (kMaxC + 1), 16);
   // wide table passes of a global-state data center: per (pod, aggregation)
   // and per edge switch maxima
