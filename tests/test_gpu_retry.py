@@ -1,0 +1,110 @@
+"""Commits that fail after the pick (the path bandwidth of a second link runs
+out although each neighbour host alone is viable), then succeed on a
+lower-ranked host or reject the request: parity with the oracle for every
+method, one block (with the pod set up ahead of each commit) and a cluster.
+The instance is built so that the failures are certain (checked on the
+oracle: the top-ranked viable host is not the one the pod ends on).  Needs a
+GPU."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1909_07673_gb300 import workloads as W
+from parity_util import check_instance
+
+pytestmark = pytest.mark.gpu
+
+K, H = 4, 16
+LINK = 100
+
+
+def _instance(method, sibling_free_cpu):
+    """k=4, 8-CPU hosts, 100 Mbps links.  Pod 0 (two 4-CPU containers) fills
+    host 0; pod 1 (one container) has a 40 Mbps link to each of them.  Edge
+    switch 0's aggregation links have 50 and 0 Mbps left, so from any host
+    outside edge switch 0 the first link fits and the second does not; host
+    1 (same edge switch, no switch link) is the only host where both fit, and
+    it is ranked last (little free CPU, CPU and memory weighted most)."""
+    pre_cpu = np.zeros(H, np.int32)
+    pre_cpu[1] = 8 - sibling_free_cpu
+    pre_link = np.zeros(3 * H, np.int32)
+    pre_link[H + 0 * 2 + 0] = 50   # edge 0 - aggregation 0: 50 left
+    pre_link[H + 0 * 2 + 1] = 100  # edge 0 - aggregation 1: nothing left
+    q = {
+        "cpu_min": np.array([4, 4, 1], np.int32), "cpu_max": np.array([4, 4, 1], np.int32),
+        "mem_min": np.array([1, 1, 1], np.int32), "mem_max": np.array([1, 1, 1], np.int32),
+        "pod": np.array([0, 0, 1], np.int32),
+        "src": np.array([0, 1], np.int32), "dst": np.array([2, 2], np.int32),
+        "bw_min": np.array([40, 40], np.int32), "bw_max": np.array([40, 40], np.int32),
+    }
+    follow = W.gen_request(np.random.default_rng(3), 6, p_edge=0.5,
+                           bw=lambda r, m: r.integers(5, 30, m))
+    weights = [0.45, 0.45, 0.025, 0.025, 0.025, 0.025]
+    return W.Instance(K, 8, 16, LINK, 6, method, W.RATIO, weights, pre_cpu,
+                      np.zeros(H, np.int32), pre_link, W.pack_requests([q, follow]))
+
+
+def _first_choice_fails(inst):
+    """On the oracle: pod 1's top-ranked viable host differs from the host
+    the request ends with (so at least one commit failed)."""
+    odc = O.OracleDC.from_instance(inst)
+    q = inst.reqs.request(0)
+    out = O.OracleDC.from_instance(inst).schedule(q)
+    pod0 = {k: v[:2] if k in ("cpu_min", "cpu_max", "mem_min", "mem_max", "pod") else v[:0]
+            for k, v in q.items()}
+    first = odc.schedule(pod0)
+    assert first["status"] == O.ACCEPTED and set(first["host"]) == {0}
+    feas, _, score = odc.rank_pod(q, 1, np.array([0, 0, -1], np.int32))
+    top = int(np.nanargmax(np.where(feas, score, np.nan)))
+    return top, out
+
+
+@pytest.fixture(scope="module")
+def ds():
+    import torch
+
+    torch.cuda.set_device(0)
+    from paper_1909_07673_gb300 import dcsched
+
+    dcsched.lib()
+    return dcsched
+
+
+@pytest.fixture(scope="module")
+def stream():
+    import torch
+
+    return torch.cuda.Stream()
+
+
+@pytest.mark.parametrize("method", [W.TOPSIS, W.AHP, W.WF])
+def test_failures_then_success(ds, stream, method):
+    inst = _instance(method, sibling_free_cpu=1)
+    top, out = _first_choice_fails(inst)
+    assert out["status"] == O.ACCEPTED and out["host"][2] == 1 and top != 1
+    dc = ds.load_instance(inst, stream=stream)
+    ds.schedule([dc])
+    check_instance(dc, inst, where="retry success m%d" % method)
+
+
+@pytest.mark.parametrize("method", [W.TOPSIS, W.AHP, W.WF])
+def test_failures_then_rejection(ds, stream, method):
+    inst = _instance(method, sibling_free_cpu=0)
+    out = O.OracleDC.from_instance(inst).schedule(inst.reqs.request(0))
+    assert out["status"] == O.REJECTED
+    dc = ds.load_instance(inst, stream=stream)
+    ds.schedule([dc])
+    check_instance(dc, inst, where="retry reject m%d" % method)
+
+
+@pytest.mark.parametrize("ncta", [2, 4])
+def test_failures_cluster(ds, stream, ncta):
+    inst = _instance(W.TOPSIS, sibling_free_cpu=1)
+    key = (inst.k, inst.n_criteria, inst.method, inst.pair_rule)
+    ds.set_launch(*key, 256, ncta)
+    try:
+        dc = ds.load_instance(inst, stream=stream)
+        ds.schedule([dc])
+        check_instance(dc, inst, where="retry cluster %d" % ncta)
+    finally:
+        ds.set_launch(*key, 0, 1)
