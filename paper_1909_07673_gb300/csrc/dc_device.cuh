@@ -117,6 +117,7 @@ struct Ctx {
   // per-column constants: FP32 for the fast path, FP64 (oracle arithmetic)
   // computed only when the guard band needs re-scoring
   float qf[kMaxC], invTf[kMaxC];
+  float mxf[kMaxC], mnf[kMaxC];  // mx / mn as floats (exact: below 2^24)
   double norm[kMaxC], Ap[kMaxC], An[kMaxC], Td[kMaxC];
   // selection
   float m1, m2;
@@ -377,7 +378,8 @@ static __device__ __forceinline__ bool same_vec(const int32_t* a, const int32_t*
 
 // FP32 fast-path selection score.  TOPSIS: the squared distances to the
 // ideal and anti-ideal, dp and dn, are formed from exact integer differences
-// scaled by q_v = W_v / sqrt(sum x^2) and accumulated with FMA; the score is
+// (criteria and extremes are integers below 2^24, so their float difference
+// is exact) scaled by q_v = W_v / sqrt(sum x^2) and accumulated with FMA; the score is
 // dn / (dp + dn), which orders hosts exactly like the closeness
 // Dn / (Dp + Dn) (both decrease with dp / dn) and needs no square root.  Its
 // relative error is <= 33 * 2^-24.  AHP RATIO: sum_v L1_v (x_v + 1) / T_v,
@@ -388,8 +390,9 @@ static __device__ __forceinline__ float score32(const Ctx& c, const int32_t* x) 
 #pragma unroll
     for (int v = 0; v < kMaxC; ++v) {
       if (v < c.C) {
-        const float a = (float)(x[v] - c.mx[v]) * c.qf[v];
-        const float b = (float)(x[v] - c.mn[v]) * c.qf[v];
+        const float xf = (float)x[v];
+        const float a = __fmul_rn(__fsub_rn(xf, c.mxf[v]), c.qf[v]);
+        const float b = __fmul_rn(__fsub_rn(xf, c.mnf[v]), c.qf[v]);
         dp = __fmaf_rn(a, a, dp);
         dn = __fmaf_rn(b, b, dn);
       }
@@ -409,8 +412,9 @@ static __device__ __forceinline__ float closeness32(const Ctx& c, const int32_t*
   if (c.method != DC_TOPSIS) return score32(c, x);
   float dp = 0.f, dn = 0.f;
   for (int v = 0; v < c.C; ++v) {
-    const float a = (float)(x[v] - c.mx[v]) * c.qf[v];
-    const float b = (float)(x[v] - c.mn[v]) * c.qf[v];
+    const float xf = (float)x[v];
+    const float a = __fmul_rn(__fsub_rn(xf, c.mxf[v]), c.qf[v]);
+    const float b = __fmul_rn(__fsub_rn(xf, c.mnf[v]), c.qf[v]);
     dp = __fmaf_rn(a, a, dp);
     dn = __fmaf_rn(b, b, dn);
   }
@@ -870,6 +874,8 @@ static __device__ void column_stats(const Sm& s) {
       // FP32 constants: q_v = W_v / sqrt(sum x^2); 1 / sum (x + 1)
       c.qf[v] = b > 0 ? __fmul_rn(c.Wf[v], __frsqrt_rn((float)b)) : 0.f;
       c.invTf[v] = __frcp_rn((float)(a + n));
+      c.mxf[v] = (float)M;
+      c.mnf[v] = (float)N;
     }
   }
   if (CL) {
@@ -900,6 +906,8 @@ static __device__ void column_stats(const Sm& s) {
         if (v == 0) c.n = n;
         c.qf[v] = b > 0 ? __fmul_rn(c.Wf[v], __frsqrt_rn((float)b)) : 0.f;
         c.invTf[v] = __frcp_rn((float)(a + n));
+        c.mxf[v] = (float)M;
+        c.mnf[v] = (float)N;
       }
     }
   }
