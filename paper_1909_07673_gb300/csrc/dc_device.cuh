@@ -155,6 +155,7 @@ struct Sm {
   int32_t *hkey, *hcnt;  // [kHash]
   int32_t* hused;        // [kHash] slots taken by the current pod (c.nhash of them)
   long long* hsum;       // [kHash] sum of bw_min of the links to that host
+  int32_t* hneed;        // [kHash] largest bw_min of the links to that host
   long long* red64;
   int32_t* red32;
   unsigned char* sel;
@@ -191,6 +192,7 @@ static __device__ __forceinline__ Sm carve(unsigned char* base, const InstDev& I
   s.hcnt = reinterpret_cast<int32_t*>(base + L.hcnt);
   s.hused = reinterpret_cast<int32_t*>(base + L.hused);
   s.hsum = reinterpret_cast<long long*>(base + L.hsum);
+  s.hneed = reinterpret_cast<int32_t*>(base + L.hneed);
   s.red64 = reinterpret_cast<long long*>(base + L.red64);
   s.red32 = reinterpret_cast<int32_t*>(base + L.red32);
   s.sel = base + L.sel;
@@ -578,6 +580,7 @@ static __device__ void pod_setup_warp(const Sm& s, const InstDev& I, int g, Pre&
         if (old == -1 || old == hv) {
           atomicAdd(&s.hcnt[h], 1);
           atomicAdd((unsigned long long*)&s.hsum[h], (unsigned long long)q.z);
+          atomicMax(&s.hneed[h], q.z);
           ins = true;
           break;
         }
@@ -641,6 +644,7 @@ static __device__ void pod_clear_warp(const Sm& s, bool ahead = false, bool trym
     s.hkey[h] = -1;
     s.hcnt[h] = 0;
     s.hsum[h] = 0;
+    s.hneed[h] = INT_MIN;
   }
   __syncwarp();
   if (lane == 0) c.nhash = 0;
@@ -648,9 +652,27 @@ static __device__ void pod_clear_warp(const Sm& s, bool ahead = false, bool trym
     for (int t = lane; t < B; t += 32) s.trymask[t] = 0u;
 }
 
+// Entry i of the neighbours folded into the switch tables: with the hash
+// complete, the i-th distinct neighbour host and the largest bw_min of its
+// links (T depends only on the host, and among the links to one host the
+// largest need gives the smallest T - need), else the i-th peer link.
+static __device__ __forceinline__ void peer_entry(const Sm& s, bool byhost, int i, int& v,
+                                                  int& need) {
+  if (byhost) {
+    const int h = s.hused[i];
+    v = s.hkey[h];
+    need = s.hneed[h];
+  } else {
+    const int4 q = s.c->pel[i];
+    v = q.y;
+    need = q.z;
+  }
+}
+
 // a2/a3 tables: T'_v[e] = min(uplink(v), best switch-path bottleneck from
-// edge switch e to edge(v)) folded over the pod's placed neighbours v.
-// Lanes are grouped per pod (gs lanes, lane a of a group = aggregation a);
+// edge switch e to edge(v)) folded over the pod's placed neighbours v (one
+// entry per neighbour host, see peer_entry; the top-2 folds give the same
+// values in any order).  Lanes are grouped per pod (gs lanes, lane a of a group = aggregation a);
 // each lane computes max_c min(ac(p, a, c), ac(pod(v), a, c)) for its a and
 // the group shares the values by shuffles.  Only the edge switches of this
 // block's pods [p0, p1) (gs divides 32, so groups never straddle warps).
@@ -668,9 +690,11 @@ static __device__ void build_tables(const Sm& s) {
     const bool active = t < tend && a < half;
     const int e = p * half + a;
     Top2 tt = {kInf, -1, kInf}, sl = {kInf, -1, kInf};
-    for (int i = 0; i < c.npe; ++i) {
-      const int4 q = c.pel[i];
-      const int v = q.y, need = q.z;
+    const bool byhost = c.hash_ok;
+    const int nent = byhost ? c.nhash : c.npe;
+    for (int i = 0; i < nent; ++i) {
+      int v, need;
+      peer_entry(s, byhost, i, v, need);
       const int ev = div_half(c, v), pv = div_half(c, ev);
       int gm = -1;
       if (active && p != pv) {
@@ -708,7 +732,7 @@ static __device__ void build_tables(const Sm& s) {
 //   G[p][a] = max_c min(ac(p, a, c), ac(pod(v), a, c))   for p != pod(v)
 //   M[e]    = max_a min(ea(e, a), ea(edge(v), a) [, G[pod(e)][a]])
 //   T       = min(uplink(v), M[e]) (no switch link when e = edge(v)),
-// folded into the top-2 tables in neighbour order like build_tables.
+// folded into the top-2 tables per neighbour entry like build_tables.
 // Only this block's pods [p0, p1).  Ends with a barrier.
 template <int B>
 static __device__ void build_tables_wide(const Sm& s) {
@@ -724,9 +748,11 @@ static __device__ void build_tables_wide(const Sm& s) {
     s.wm[el] = -1;
   }
   __syncthreads();
-  for (int i = 0; i < c.npe; ++i) {
-    const int4 q = c.pel[i];
-    const int v = q.y, need = q.z;
+  const bool byhost = c.hash_ok;
+  const int nent = byhost ? c.nhash : c.npe;
+  for (int i = 0; i < nent; ++i) {
+    int v, need;
+    peer_entry(s, byhost, i, v, need);
     const int ev = div_half(c, v), pv = div_half(c, ev);
     // pass 1: (pod, aggregation, core) triples of this block; consecutive
     // threads take consecutive aggregation switches (contiguous link slots,
@@ -1812,6 +1838,7 @@ static __device__ void load_instance(const Sm& s, const InstDev& I) {
     s.hkey[h] = -1;
     s.hcnt[h] = 0;
     s.hsum[h] = 0;
+    s.hneed[h] = INT_MIN;
   }
   if (tid == 0) c.nhash = 0;
   s.tmark[tid] = 0;

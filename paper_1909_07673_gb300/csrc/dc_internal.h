@@ -129,7 +129,7 @@ DC_HD inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Shared-memory layout of one scheduling block (bytes), see dc_kernels.cu.
 struct SmemLayout {
-  size_t ctx, cm, ctr, lk, tab, cp, tmark, trymask, hkey, hcnt, hused, hsum, red64, red32, sel;
+  size_t ctx, cm, ctr, lk, tab, cp, tmark, trymask, hkey, hcnt, hused, hsum, hneed, red64, red32, sel;
   size_t st_pc, st_pe, st_hof, pel, curc, pel2, curc2, xwarp, wide, total;
 };
 
@@ -160,6 +160,7 @@ DC_HD inline SmemLayout smem_layout(int k, int block, size_t ctx_bytes, bool sta
   L.hcnt = o; o = align_up(o + 4 * (size_t)kHash, 16);
   L.hused = o; o = align_up(o + 4 * (size_t)kHash, 16);
   L.hsum = o; o = align_up(o + 8 * (size_t)kHash, 16);
+  L.hneed = o; o = align_up(o + 4 * (size_t)kHash, 16);
   L.red64 = o; o = align_up(o + 8 * nw * 2 * kMaxC, 16);
   L.red32 = o; o = align_up(o + 4 * nw * (2 * kMaxC + 1), 16);
   L.sel = o; o = align_up(o + 16 * nw, 16);
