@@ -358,36 +358,64 @@ int store_request(dc_t* d, const dc_request* q) {
   if ((n > 0 && (!q->cpu_min || !q->cpu_max || !q->mem_min || !q->mem_max || !q->pod)) ||
       (m > 0 && (!q->src || !q->dst || !q->bw_min || !q->bw_max)))
     return DC_E_INVAL;
+  // containers: validation, pod count, and whether every container is its
+  // own pod in index order (then the container layout is the identity)
   int32_t P = 0;
+  bool ident = true;
   for (int32_t i = 0; i < n; ++i) {
-    if (q->pod[i] < 0 || q->pod[i] >= n) return DC_E_INVAL;
+    const int32_t g = q->pod[i];
+    if (g < 0 || g >= n) return DC_E_INVAL;
     if (q->cpu_min[i] < 0 || q->cpu_min[i] > q->cpu_max[i] || q->cpu_max[i] > 65535) return DC_E_INVAL;
     if (q->mem_min[i] < 0 || q->mem_min[i] > q->mem_max[i] || q->mem_max[i] > 65535) return DC_E_INVAL;
-    P = std::max(P, q->pod[i] + 1);
+    P = std::max(P, g + 1);
+    ident = ident && g == i;
   }
-  std::vector<int32_t> pc(P + 1, 0), pe(P + 1, 0), npeer(P, 0);
-  for (int32_t i = 0; i < n; ++i) pc[q->pod[i] + 1] += 1;
-  for (int32_t g = 0; g < P; ++g)
-    if (pc[g + 1] == 0) return DC_E_INVAL;  // pod ids must be dense
+  // per-thread scratch, reused across calls (instances on other threads
+  // have their own)
+  thread_local std::vector<int32_t> pc, pe, npeer, fill;
+  pc.assign(P + 1, 0);
+  pe.assign(P + 1, 0);
+  npeer.assign(P, 0);
+  if (ident) {
+    for (int32_t g = 0; g < P; ++g) pc[g + 1] = 1;
+  } else {
+    for (int32_t i = 0; i < n; ++i) pc[q->pod[i] + 1] += 1;
+    for (int32_t g = 0; g < P; ++g)
+      if (pc[g + 1] == 0) return DC_E_INVAL;  // pod ids must be dense
+  }
   for (int32_t e = 0; e < m; ++e) {
-    if (q->src[e] < 0 || q->src[e] >= n || q->dst[e] < 0 || q->dst[e] >= n) return DC_E_INVAL;
-    if (q->src[e] == q->dst[e]) return DC_E_INVAL;
+    const int32_t a = q->src[e], b = q->dst[e];
+    if (a < 0 || a >= n || b < 0 || b >= n || a == b) return DC_E_INVAL;
     if (q->bw_min[e] < 0 || q->bw_min[e] > q->bw_max[e]) return DC_E_INVAL;
-    const int32_t later = std::max(q->pod[q->src[e]], q->pod[q->dst[e]]);
+    const int32_t ps = q->pod[a], pt = q->pod[b];
+    const int32_t later = std::max(ps, pt);
     pe[later + 1] += 1;
-    if (q->pod[q->src[e]] != q->pod[q->dst[e]]) npeer[later] += 1;
+    npeer[later] += ps != pt;
   }
   int32_t max_pe = 0;
-  for (int32_t g = 0; g < P; ++g) max_pe = std::max(max_pe, npeer[g]);
   for (int32_t g = 0; g < P; ++g) {
+    max_pe = std::max(max_pe, npeer[g]);
     pc[g + 1] += pc[g];
     pe[g + 1] += pe[g];
   }
-  std::vector<int4> cl(n), el(m);
-  std::vector<int32_t> fillc(pc.begin(), pc.end() - 1), fille(pe.begin(), pe.end() - 1);
-  for (int32_t i = 0; i < n; ++i)
-    cl[fillc[q->pod[i]]++] = make_int4(i, q->cpu_min[i] | (q->cpu_max[i] << 16),
-                                       q->mem_min[i] | (q->mem_max[i] << 16), 0);
+  // the request is valid: lay it out directly in the pinned arenas
+  DC_TRY(d->c_lay.reserve(d->c_lay.n + n));
+  DC_TRY(d->e_lay.reserve(d->e_lay.n + m));
+  DC_TRY(d->p_coff.reserve(d->p_coff.n + P + 1));
+  DC_TRY(d->p_eoff.reserve(d->p_eoff.n + P + 1));
+  DC_TRY(d->reqs.reserve(d->reqs.n + 1));
+  int4* cl = d->c_lay.p + d->c_lay.n;
+  if (ident) {
+    for (int32_t i = 0; i < n; ++i)
+      cl[i] = make_int4(i, q->cpu_min[i] | (q->cpu_max[i] << 16), q->mem_min[i] | (q->mem_max[i] << 16), 0);
+  } else {
+    fill.assign(pc.begin(), pc.end() - 1);
+    for (int32_t i = 0; i < n; ++i)
+      cl[fill[q->pod[i]]++] = make_int4(i, q->cpu_min[i] | (q->cpu_max[i] << 16),
+                                        q->mem_min[i] | (q->mem_max[i] << 16), 0);
+  }
+  int4* el = d->e_lay.p + d->e_lay.n;
+  fill.assign(pe.begin(), pe.end() - 1);
   for (int32_t e = 0; e < m; ++e) {
     const int32_t ps = q->pod[q->src[e]], pt = q->pod[q->dst[e]];
     int32_t w = e, other;
@@ -400,12 +428,14 @@ int store_request(dc_t* d, const dc_request* q) {
     } else {
       other = q->src[e];
     }
-    el[fille[std::max(ps, pt)]++] = make_int4(w, other, q->bw_min[e], q->bw_max[e]);
+    el[fill[std::max(ps, pt)]++] = make_int4(w, other, q->bw_min[e], q->bw_max[e]);
   }
-  DC_TRY(d->c_lay.append(cl.data(), n));
-  DC_TRY(d->e_lay.append(el.data(), m));
-  DC_TRY(d->p_coff.append(pc.data(), P + 1));
-  DC_TRY(d->p_eoff.append(pe.data(), P + 1));
+  std::memcpy(d->p_coff.p + d->p_coff.n, pc.data(), (P + 1) * sizeof(int32_t));
+  std::memcpy(d->p_eoff.p + d->p_eoff.n, pe.data(), (P + 1) * sizeof(int32_t));
+  d->c_lay.n += n;
+  d->e_lay.n += m;
+  d->p_coff.n += P + 1;
+  d->p_eoff.n += P + 1;
   ReqRec r{};
   r.c_off = d->tot_c;
   r.e_off = d->tot_e;
@@ -415,7 +445,7 @@ int store_request(dc_t* d, const dc_request* q) {
   r.n_e = m;
   r.n_p = P;
   r.max_pe = max_pe;
-  DC_TRY(d->reqs.append(&r, 1));
+  d->reqs.p[d->reqs.n++] = r;
   d->tot_c += n;
   d->tot_e += m;
   d->tot_p += P;
