@@ -52,6 +52,9 @@ def parse():
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--requests", type=int, default=100, help="requests per data center")
     ap.add_argument("--instances", type=int, default=256)
+    ap.add_argument("--only-k", type=int, nargs="+", default=None,
+                    help="keep only the data centers of these fat-tree sizes (the same "
+                         "instances as in the full workload)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--serving-events", type=int, default=0,
@@ -84,16 +87,23 @@ def parse():
 
 def workload(args, rank):
     from paper_1909_07673_gb300 import workloads as W
-    return W.batched(seed=4 + 1000 * rank, n_instances=args.instances, n_requests=args.requests)
+    wl = W.batched(seed=4 + 1000 * rank, n_instances=args.instances, n_requests=args.requests)
+    if getattr(args, "only_k", None):
+        wl = W.Workload(wl.name, [i for i in wl.instances if i.k in args.only_k])
+        if not wl.instances:
+            raise SystemExit("--only-k: no data center of those sizes")
+    return wl
 
 
 def config_dict(args, wl, world):
     hosts = sum(i.hosts for i in wl.instances)
+    n = len(wl.instances)
+    ks = "/".join(str(k) for k in sorted({i.k for i in wl.instances}))
     return {
-        "workload": "batched fat-tree DCs: %d instances (k 8/16/24/32), %d requests of 4-256 "
-                    "containers each, TOPSIS, 6 criteria" % (args.instances, args.requests),
-        "instances_per_gpu": args.instances,
-        "requests_per_gpu": args.instances * args.requests,
+        "workload": "batched fat-tree DCs: %d instances (k %s), %d requests of 4-256 "
+                    "containers each, TOPSIS, 6 criteria" % (n, ks, args.requests),
+        "instances_per_gpu": n,
+        "requests_per_gpu": n * args.requests,
         "hosts_per_gpu": hosts,
         "method": "TOPSIS",
         "l2": "flushed before every step (256 MiB device write); request inputs exceed L2",
