@@ -332,7 +332,8 @@ static __device__ __forceinline__ bool commit_possible(const Sm& s, int u) {
 // with 6 criteria c4 = smallest bottleneck to the pod's placed neighbours
 // (link capacity for a neighbour on u itself, c3 without neighbours) and
 // c5 = sum over the pod's links to placed neighbours of (6 - hops).
-template <int B>
+// CC: the number of criteria when fixed at compile time (0: c.C).
+template <int B, int CC = 0>
 static __device__ __forceinline__ bool host_crit(const Sm& s, int u, int32_t* x) {
   const Ctx& c = *s.c;
   const uint32_t cm = s.cm[u];
@@ -357,7 +358,7 @@ static __device__ __forceinline__ bool host_crit(const Sm& s, int u, int32_t* x)
     const int Bn = s.Be[e], Cn = s.Cp[p];
     c5 = 6 * A + 4 * (Bn - A) + 2 * (Cn - Bn);
   }
-  if (c.C == 6) {
+  if (CC == 6 || (CC == 0 && c.C == 6)) {
     x[4] = c4;
     x[5] = c5;
   }
@@ -386,12 +387,14 @@ static __device__ __forceinline__ bool same_vec(const int32_t* a, const int32_t*
 // Dn / (Dp + Dn) (both decrease with dp / dn) and needs no square root.  Its
 // relative error is <= 33 * 2^-24.  AHP RATIO: sum_v L1_v (x_v + 1) / T_v,
 // relative error <= 11 * 2^-24.
+template <int CC = 0, int TP = 0>
 static __device__ __forceinline__ float score32(const Ctx& c, const int32_t* x) {
-  if (c.method == DC_TOPSIS) {
+  const int C = CC ? CC : c.C;
+  if (TP || c.method == DC_TOPSIS) {
     float dp = 0.f, dn = 0.f;
 #pragma unroll
     for (int v = 0; v < kMaxC; ++v) {
-      if (v < c.C) {
+      if (v < C) {
         const float xf = (float)x[v];
         const float a = __fmul_rn(__fsub_rn(xf, c.mxf[v]), c.qf[v]);
         const float b = __fmul_rn(__fsub_rn(xf, c.mnf[v]), c.qf[v]);
@@ -405,7 +408,7 @@ static __device__ __forceinline__ float score32(const Ctx& c, const int32_t* x) 
   float acc = 0.f;
 #pragma unroll
   for (int v = 0; v < kMaxC; ++v)
-    if (v < c.C) acc = __fmaf_rn(c.L1f[v], __fmul_rn((float)(x[v] + 1), c.invTf[v]), acc);
+    if (v < C) acc = __fmaf_rn(c.L1f[v], __fmul_rn((float)(x[v] + 1), c.invTf[v]), acc);
   return acc;
 }
 
@@ -803,25 +806,18 @@ static __device__ __forceinline__ void tables(const Sm& s, const InstDev& I) {
     build_tables<B>(s);
 }
 
-// a4: exact column statistics over the viable hosts and FP32 constants.
-// In a cluster every block reduces its own hosts, publishes the partial
-// statistics and then combines those of all blocks (exact integers, so all
-// blocks obtain the same values).
-template <int B, bool CL>
-static __device__ void column_stats(const Sm& s) {
-  Ctx& c = *s.c;
-  const int tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
-  constexpr int NW = B / 32;
-  const int C = c.C;
-  uint32_t cnt = 0;
-  uint32_t s1[kMaxC];
-  unsigned long long s2[kMaxC];
-  int mx[kMaxC], mn[kMaxC];
-#pragma unroll
-  for (int v = 0; v < kMaxC; ++v) { s1[v] = 0; s2[v] = 0; mx[v] = INT_MIN; mn[v] = INT_MAX; }
+// The host scan of column_stats: this thread's viable hosts folded into its
+// count, sums, sums of squares and extremes (CC: criteria count fixed at
+// compile time, 0: c.C).
+template <int B, bool CL, int CC>
+static __device__ __forceinline__ void stats_scan(const Sm& s, uint32_t& cnt, uint32_t* s1,
+                                                  unsigned long long* s2, int* mx, int* mn) {
+  const Ctx& c = *s.c;
+  const int tid = threadIdx.x;
+  const int C = CC ? CC : c.C;
   auto visit = [&](int u) {
     int32_t x[kMaxC];
-    if (host_crit<B>(s, u, x)) {
+    if (host_crit<B, CC>(s, u, x)) {
       ++cnt;
 #pragma unroll
       for (int v = 0; v < kMaxC; ++v) {
@@ -843,6 +839,28 @@ static __device__ void column_stats(const Sm& s) {
 #pragma unroll 1
     for (int u = c.h0 + tid; u < c.h1; u += B) visit(u);
   }
+}
+
+// a4: exact column statistics over the viable hosts and FP32 constants.
+// In a cluster every block reduces its own hosts, publishes the partial
+// statistics and then combines those of all blocks (exact integers, so all
+// blocks obtain the same values).
+template <int B, bool CL>
+static __device__ void column_stats(const Sm& s) {
+  Ctx& c = *s.c;
+  const int tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
+  constexpr int NW = B / 32;
+  const int C = c.C;
+  uint32_t cnt = 0;
+  uint32_t s1[kMaxC];
+  unsigned long long s2[kMaxC];
+  int mx[kMaxC], mn[kMaxC];
+#pragma unroll
+  for (int v = 0; v < kMaxC; ++v) { s1[v] = 0; s2[v] = 0; mx[v] = INT_MIN; mn[v] = INT_MAX; }
+  if (C == 6)
+    stats_scan<B, CL, 6>(s, cnt, s1, s2, mx, mn);
+  else
+    stats_scan<B, CL, 0>(s, cnt, s1, s2, mx, mn);
   // warp level: 32-bit redux (sum of squares split in 24-bit halves)
   const uint32_t wc = __reduce_add_sync(0xffffffffu, cnt);
 #pragma unroll
@@ -1124,11 +1142,11 @@ constexpr int kXw = kMaxC + 1;
 
 // FP32 selection score of host u, or -1 when u is not viable, its commit
 // must fail, or it failed a commit already.
-template <int B>
+template <int B, int CC = 0, int TP = 0>
 static __device__ __forceinline__ float cand_score(const Sm& s, int u, int32_t* x) {
   if ((s.trymask[u % B] >> (u / B)) & 1u) return -1.f;
-  if (!host_crit<B>(s, u, x) || !commit_possible<B>(s, u)) return -1.f;
-  return score32(*s.c, x);
+  if (!host_crit<B, CC>(s, u, x) || !commit_possible<B>(s, u)) return -1.f;
+  return score32<CC, TP>(*s.c, x);
 }
 
 // Criteria of the leader of a reduction: `ow` is the lane whose partial
@@ -1139,31 +1157,16 @@ static __device__ __forceinline__ int owner_lane(bool has) {
   return m ? __ffs(m) - 1 : 0;
 }
 
-// a5/a6: FP32 scores of every candidate fused with the block argmax, then
-// certification.  Sets c.winner (-1 when no candidate remains) and c.xw, the
-// winner's criteria.  One pass: every thread keeps the Lead of its hosts
-// (leader criteria included), warps and blocks combine Leads, so ties at the
-// maximum are certified without another pass (they are, when every host at
-// the maximum carries the leader's criteria).  In a cluster each block
-// reduces its own hosts and the blocks' Leads are combined; every branch
-// below depends only on combined values, so all blocks take it together.
-template <int B, bool CL>
-static __device__ void pick_host(const Sm& s) {
-  Ctx& c = *s.c;
-  const int tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
-  constexpr int NW = B / 32;
-  const int C = c.C;
-  Lead me;
-  me.m1 = -1.f;
-  me.m2 = -1.f;
-  me.idx = INT_MAX;
-  me.cnt = 0;
-  me.mixed = false;
-#pragma unroll
-  for (int v = 0; v < kMaxC; ++v) me.x[v] = 0;
+// The candidate scan of pick_host: every host of this thread, in increasing
+// index, folded into the thread's Lead.
+template <int B, bool CL, int CC, int TP>
+static __device__ __forceinline__ void pick_scan(const Sm& s, Lead& me) {
+  const Ctx& c = *s.c;
+  const int tid = threadIdx.x;
+  const int C = CC ? CC : c.C;
   auto visit = [&](int u) {
     int32_t x[kMaxC];
-    const float sc = cand_score<B>(s, u, x);
+    const float sc = cand_score<B, CC, TP>(s, u, x);
     // hosts are visited in increasing index: an equal score keeps the leader
     if (sc > me.m1) {
       me.m2 = me.m1;
@@ -1189,6 +1192,36 @@ static __device__ void pick_host(const Sm& s) {
 #pragma unroll 1
     for (int u = c.h0 + tid; u < c.h1; u += B) visit(u);
   }
+}
+
+// a5/a6: FP32 scores of every candidate fused with the block argmax, then
+// certification.  Sets c.winner (-1 when no candidate remains) and c.xw, the
+// winner's criteria.  One pass: every thread keeps the Lead of its hosts
+// (leader criteria included), warps and blocks combine Leads, so ties at the
+// maximum are certified without another pass (they are, when every host at
+// the maximum carries the leader's criteria).  In a cluster each block
+// reduces its own hosts and the blocks' Leads are combined; every branch
+// below depends only on combined values, so all blocks take it together.
+template <int B, bool CL>
+static __device__ void pick_host(const Sm& s) {
+  Ctx& c = *s.c;
+  const int tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
+  constexpr int NW = B / 32;
+  const int C = c.C;
+  Lead me;
+  me.m1 = -1.f;
+  me.m2 = -1.f;
+  me.idx = INT_MAX;
+  me.cnt = 0;
+  me.mixed = false;
+#pragma unroll
+  for (int v = 0; v < kMaxC; ++v) me.x[v] = 0;
+  // the common configuration (6 criteria, TOPSIS) with both fixed at
+  // compile time, every other one with the generic loop
+  if (C == 6 && c.method == DC_TOPSIS)
+    pick_scan<B, CL, 6, 1>(s, me);
+  else
+    pick_scan<B, CL, 0, 0>(s, me);
   Lead wl = lead_warp(me, C);
   Sel* ws = reinterpret_cast<Sel*>(s.sel);
   if (lane == 0) {
