@@ -679,11 +679,13 @@ static __device__ __forceinline__ void peer_entry(const Sm& s, bool byhost, int 
 // each lane computes max_c min(ac(p, a, c), ac(pod(v), a, c)) for its a and
 // the group shares the values by shuffles.  Only the edge switches of this
 // block's pods [p0, p1) (gs divides 32, so groups never straddle warps).
-// Ends with a barrier.
-template <int B>
+// Ends with a barrier.  HALF: k / 2 fixed at compile time (loops fully
+// unrolled), 0: c.half.
+template <int B, int HALF>
 static __device__ void build_tables(const Sm& s) {
   const Ctx& c = *s.c;
-  const int half = c.half, gs = c.gs;
+  const int half = HALF ? HALF : c.half;
+  const int gs = HALF ? (HALF <= 4 ? 4 : HALF <= 8 ? 8 : HALF <= 16 ? 16 : 32) : c.gs;
   const int lane = lane_id();
   const int gbase = lane & ~(gs - 1);
   const int tend = c.p1 * gs;
@@ -701,10 +703,12 @@ static __device__ void build_tables(const Sm& s) {
       const int ev = div_half(c, v), pv = div_half(c, ev);
       int gm = -1;
       if (active && p != pv) {
+#pragma unroll
         for (int cc = 0; cc < half; ++cc)
           gm = imax(gm, imin(s.lk[s_ac(c, p * half + a, cc)], s.lk[s_ac(c, pv * half + a, cc)]));
       }
       int mid = -1;
+#pragma unroll
       for (int a2 = 0; a2 < half; ++a2) {
         const int g2 = __shfl_sync(0xffffffffu, gm, gbase + a2);
         if (active) {
@@ -800,10 +804,18 @@ static __device__ void build_tables_wide(const Sm& s) {
 // block holds few pods (measured: up to 12), else the per-lane form.
 template <int B>
 static __device__ __forceinline__ void tables(const Sm& s, const InstDev& I) {
-  if (I.state_global && s.c->p1 - s.c->p0 <= 12)
+  if (I.state_global && s.c->p1 - s.c->p0 <= 12) {
     build_tables_wide<B>(s);
-  else
-    build_tables<B>(s);
+    return;
+  }
+  // the common fat-tree sizes with k / 2 fixed at compile time
+  switch (s.c->half) {
+    case 4: build_tables<B, 4>(s); break;
+    case 8: build_tables<B, 8>(s); break;
+    case 12: build_tables<B, 12>(s); break;
+    case 16: build_tables<B, 16>(s); break;
+    default: build_tables<B, 0>(s); break;
+  }
 }
 
 // The host scan of column_stats: this thread's viable hosts folded into its
