@@ -102,6 +102,7 @@ struct Ctx {
   int32_t pel_smem;   // peer links in shared memory (both copies)
   // pod
   long long dmin_cpu, dmax_cpu, dmin_mem, dmax_mem;
+  int32_t dmin_cpu32, dmin_mem32;  // the minima clamped to INT_MAX (free amounts are < 2^16)
   int32_t size, npe;
   int32_t need1, need1h, need2;
   int32_t hash_ok;
@@ -110,6 +111,8 @@ struct Ctx {
   // commit prefilter (exact necessary condition, see commit_possible)
   long long bw_total;  // sum of bw_min over the pod's links to placed containers
   int32_t n_over, h_over;  // neighbour hosts whose uplink cannot carry their links
+  int32_t only_host;       // -1: any host may commit, -2: none, else only that host
+  uint32_t bwt32;          // bw_total clamped to 2^31 (above every link residual)
   // column statistics over the viable hosts
   int32_t n;
   long long S1[kMaxC], S2[kMaxC];
@@ -318,9 +321,12 @@ template <int B>
 static __device__ __forceinline__ bool commit_possible(const Sm& s, int u) {
   const Ctx& c = *s.c;
   if (c.npe == 0 || !c.hash_ok) return true;
-  if (c.n_over > 1 || (c.n_over == 1 && u != c.h_over)) return false;
+  if (c.only_host != -1 && c.only_host != u) return false;
+  const bool isp = (s.tmark[u % B] >> (u / B)) & 1u;
+  // residuals are >= 0: a 32-bit compare against the clamped total
+  if (!isp) return (uint32_t)s.lk[u] >= c.bwt32;
   long long on_u = 0;
-  if ((s.tmark[u % B] >> (u / B)) & 1u) {
+  {
     const int slot = peer_slot(s, u);
     if (slot >= 0) on_u = s.hsum[slot];
   }
@@ -340,7 +346,7 @@ static __device__ __forceinline__ bool host_crit(const Sm& s, int u, int32_t* x)
   const int cpu = (int)(cm & 0xffffu), mem = (int)(cm >> 16);
   const int ctr = s.ctr[u];
   const int up = s.lk[u];
-  bool f = cpu >= c.dmin_cpu && mem >= c.dmin_mem;
+  bool f = cpu >= c.dmin_cpu32 && mem >= c.dmin_mem32;
   x[0] = cpu;
   x[1] = mem;
   x[2] = ((ctr & kCtrMask) > 0 || (ctr & kPreBit)) ? 1 : 0;
@@ -515,6 +521,8 @@ static __device__ void pod_uplink_check_warp(const Sm& s) {
     c.bw_total = tot;
     c.n_over = n_over;
     c.h_over = h_over;
+    c.only_host = n_over == 0 ? -1 : (n_over == 1 ? h_over : -2);
+    c.bwt32 = (uint32_t)(tot < (1ll << 31) ? tot : (1ll << 31));
   }
   __syncwarp();
 }
@@ -604,6 +612,8 @@ static __device__ void pod_setup_warp(const Sm& s, const InstDev& I, int g, Pre&
   if (lane == 0) {
     c.dmin_cpu = dmin_c;
     c.dmin_mem = dmin_m;
+    c.dmin_cpu32 = (int32_t)(dmin_c < INT_MAX ? dmin_c : INT_MAX);
+    c.dmin_mem32 = (int32_t)(dmin_m < INT_MAX ? dmin_m : INT_MAX);
     c.need1 = nd.v1;
     c.need1h = nd.h1;
     c.need2 = nd.v2;
