@@ -317,12 +317,12 @@ static __device__ int peer_links_on(const Sm& s, int u) {
 // first successful candidate unchanged): every path from u to a neighbour
 // on another host starts with u's host link and every path to neighbour v
 // ends with v's host link, and each link reserves at least bw^min.
+// isp: u hosts one of the pod's placed neighbours (its bit in s.tmark).
 template <int B>
-static __device__ __forceinline__ bool commit_possible(const Sm& s, int u) {
+static __device__ __forceinline__ bool commit_possible(const Sm& s, int u, bool isp) {
   const Ctx& c = *s.c;
   if (c.npe == 0 || !c.hash_ok) return true;
   if (c.only_host != -1 && c.only_host != u) return false;
-  const bool isp = (s.tmark[u % B] >> (u / B)) & 1u;
   // residuals are >= 0: a 32-bit compare against the clamped total
   if (!isp) return (uint32_t)s.lk[u] >= c.bwt32;
   long long on_u = 0;
@@ -332,15 +332,20 @@ static __device__ __forceinline__ bool commit_possible(const Sm& s, int u) {
   }
   return (long long)s.lk[u] >= c.bw_total - on_u;
 }
+template <int B>
+static __device__ __forceinline__ bool commit_possible(const Sm& s, int u) {
+  return commit_possible<B>(s, u, (s.tmark[u % B] >> (u / B)) & 1u);
+}
 
 // Criteria of host u (integers, all benefit criteria) and its viability.
 // c0 free CPU, c1 free memory, c2 active flag f_u, c3 uplink residual;
 // with 6 criteria c4 = smallest bottleneck to the pod's placed neighbours
 // (link capacity for a neighbour on u itself, c3 without neighbours) and
 // c5 = sum over the pod's links to placed neighbours of (6 - hops).
-// CC: the number of criteria when fixed at compile time (0: c.C).
+// CC: the number of criteria when fixed at compile time (0: c.C); isp: u
+// hosts one of the pod's placed neighbours (its bit in s.tmark).
 template <int B, int CC = 0>
-static __device__ __forceinline__ bool host_crit(const Sm& s, int u, int32_t* x) {
+static __device__ __forceinline__ bool host_crit(const Sm& s, int u, int32_t* x, bool isp) {
   const Ctx& c = *s.c;
   const uint32_t cm = s.cm[u];
   const int cpu = (int)(cm & 0xffffu), mem = (int)(cm >> 16);
@@ -349,12 +354,11 @@ static __device__ __forceinline__ bool host_crit(const Sm& s, int u, int32_t* x)
   bool f = cpu >= c.dmin_cpu32 && mem >= c.dmin_mem32;
   x[0] = cpu;
   x[1] = mem;
-  x[2] = ((ctr & kCtrMask) > 0 || (ctr & kPreBit)) ? 1 : 0;
+  x[2] = ctr != 0 ? 1 : 0;  // a container count or the pre-load bit
   x[3] = up;
   int c4 = up, c5 = 0;
   if (c.npe > 0) {
     const int e = div_half(c, u), p = div_half(c, e);
-    const bool isp = (s.tmark[u % B] >> (u / B)) & 1u;
     const int Tx = (isp && s.T1h[e] == u) ? s.T2[e] : s.T1[e];
     const int Sx = (isp && s.S1h[e] == u) ? s.S2[e] : s.S1[e];
     const int Nx = (isp && c.need1h == u) ? c.need2 : c.need1;
@@ -369,6 +373,10 @@ static __device__ __forceinline__ bool host_crit(const Sm& s, int u, int32_t* x)
     x[5] = c5;
   }
   return f;
+}
+template <int B, int CC = 0>
+static __device__ __forceinline__ bool host_crit(const Sm& s, int u, int32_t* x) {
+  return host_crit<B, CC>(s, u, x, (s.tmark[u % B] >> (u / B)) & 1u);
 }
 
 // Out-of-line copy for the rare certification paths (keeps code size down).
@@ -837,9 +845,10 @@ static __device__ __forceinline__ void stats_scan(const Sm& s, uint32_t& cnt, ui
   const Ctx& c = *s.c;
   const int tid = threadIdx.x;
   const int C = CC ? CC : c.C;
+  const uint32_t tmw = s.tmark[(c.h0 + tid) % B];  // u % B is fixed for this thread
   auto visit = [&](int u) {
     int32_t x[kMaxC];
-    if (host_crit<B, CC>(s, u, x)) {
+    if (host_crit<B, CC>(s, u, x, (tmw >> (u / B)) & 1u)) {
       ++cnt;
 #pragma unroll
       for (int v = 0; v < kMaxC; ++v) {
@@ -1164,11 +1173,18 @@ constexpr int kXw = kMaxC + 1;
 
 // FP32 selection score of host u, or -1 when u is not viable, its commit
 // must fail, or it failed a commit already.
+// isp / tried: u's bits in s.tmark / s.trymask.
+template <int B, int CC = 0, int TP = 0>
+static __device__ __forceinline__ float cand_score(const Sm& s, int u, int32_t* x, bool isp,
+                                                   bool tried) {
+  if (tried) return -1.f;
+  if (!host_crit<B, CC>(s, u, x, isp) || !commit_possible<B>(s, u, isp)) return -1.f;
+  return score32<CC, TP>(*s.c, x);
+}
 template <int B, int CC = 0, int TP = 0>
 static __device__ __forceinline__ float cand_score(const Sm& s, int u, int32_t* x) {
-  if ((s.trymask[u % B] >> (u / B)) & 1u) return -1.f;
-  if (!host_crit<B, CC>(s, u, x) || !commit_possible<B>(s, u)) return -1.f;
-  return score32<CC, TP>(*s.c, x);
+  return cand_score<B, CC, TP>(s, u, x, (s.tmark[u % B] >> (u / B)) & 1u,
+                               (s.trymask[u % B] >> (u / B)) & 1u);
 }
 
 // Criteria of the leader of a reduction: `ow` is the lane whose partial
@@ -1186,9 +1202,13 @@ static __device__ __forceinline__ void pick_scan(const Sm& s, Lead& me) {
   const Ctx& c = *s.c;
   const int tid = threadIdx.x;
   const int C = CC ? CC : c.C;
+  // every host u = h0 + tid + j * B of this thread has its mask bits in the
+  // same word (u % B is fixed), bit u / B
+  const uint32_t tmw = s.tmark[(c.h0 + tid) % B], tyw = s.trymask[(c.h0 + tid) % B];
   auto visit = [&](int u) {
     int32_t x[kMaxC];
-    const float sc = cand_score<B, CC, TP>(s, u, x);
+    const int j = u / B;
+    const float sc = cand_score<B, CC, TP>(s, u, x, (tmw >> j) & 1u, (tyw >> j) & 1u);
     // hosts are visited in increasing index: an equal score keeps the leader
     if (sc > me.m1) {
       me.m2 = me.m1;
