@@ -142,6 +142,8 @@ struct Ctx {
   int32_t fit, wf;     // best fit / worst fit (fit = 1; wf = 1 for worst fit)
   int32_t hcpu, hmem;  // host capacities
   int32_t gstate;    // the state lives in global memory
+  int32_t pref_regs;  // the next pod's first records are prefetched into registers
+                      // (cluster / global state); else an L2 prefetch hint
   int32_t hof_smem;  // hof is this block's shared copy
   Xch xs;
 };
@@ -491,6 +493,17 @@ static __device__ __noinline__ double score64(int method, int C, const double* W
 // first 32 links of the pod's groups).
 struct Pre { int4 c, e; };
 
+// L2 prefetch of the records pod g's set-up reads first (no register waits
+// on it; the one-block kernel's set-up ahead loads them itself).
+static __device__ __forceinline__ void prefetch_pod_l2(const Ctx& c, const InstDev& I, int g) {
+  const int lane = lane_id();
+  if (g < c.n_p) {
+    const int c0 = c.pc[g], c1 = c.pc[g + 1], e0 = c.pe[g], e1 = c.pe[g + 1];
+    if (c0 + lane < c1) asm volatile("prefetch.L2 [%0];" ::"l"(I.c_lay + c.c_off + c0 + lane));
+    if (e0 + lane < e1) asm volatile("prefetch.L2 [%0];" ::"l"(I.e_lay + c.e_off + e0 + lane));
+  }
+}
+
 static __device__ __forceinline__ Pre prefetch_pod(const Ctx& c, const InstDev& I, int g) {
   const int lane = lane_id();
   Pre p = {make_int4(0, 0, 0, 0), make_int4(0, 0, 0, 0)};
@@ -542,15 +555,18 @@ static __device__ void pod_uplink_check_warp(const Sm& s) {
 enum { kSetupAhead = 1, kSetupFromGlobal = 2 };
 
 // a1: pod demand and the pod's links to containers of earlier pods (one
-// warp).  `cur` holds the pod's prefetched records; on return `cur` holds
-// those of pod g + 1.
+// warp).  With c.pref_regs `cur` holds the pod's prefetched records and on
+// return those of pod g + 1; otherwise the records are loaded here and pod
+// g + 1's are only prefetched into L2 (in the one-block kernel the set-up
+// runs beside the commit, where the load latency is hidden, and a register
+// prefetch would make the warp wait for it at its next register move).
 template <int B>
 static __device__ void pod_setup_warp(const Sm& s, const InstDev& I, int g, Pre& cur,
                                       int mode = 0) {
   Ctx& c = *s.c;
   const int lane = lane_id();
   const bool ahead = mode & kSetupAhead;
-  const bool pre = !(mode & kSetupFromGlobal);
+  const bool pre = c.pref_regs && !(mode & kSetupFromGlobal);
   int4* curc = ahead ? c.curc_n : c.curc;
   int4* pel = ahead ? c.pel_n : c.pel;
   const int32_t c0 = c.pc[g], c1 = c.pc[g + 1];
@@ -641,7 +657,10 @@ static __device__ void pod_setup_warp(const Sm& s, const InstDev& I, int g, Pre&
   }
   __syncwarp();
   if (!ahead) pod_uplink_check_warp(s);
-  cur = prefetch_pod(c, I, g + 1);
+  if (c.pref_regs)
+    cur = prefetch_pod(c, I, g + 1);
+  else
+    prefetch_pod_l2(c, I, g + 1);
   __syncwarp();
 }
 
@@ -1877,6 +1896,7 @@ static __device__ void load_instance(const Sm& s, const InstDev& I) {
     c.h0 = c.p0 * I.half * I.half;
     c.h1 = c.p1 * I.half * I.half;
     c.gstate = I.state_global;
+    c.pref_regs = (CL || I.state_global) ? 1 : 0;
     c.fit = (I.method == DC_BF || I.method == DC_WF) ? 1 : 0;
     c.wf = I.method == DC_WF ? 1 : 0;
     c.hcpu = I.host_cpu;
@@ -2164,7 +2184,7 @@ static __device__ void schedule_request(const Sm& s, const InstDev& I, int r) {
   // warp 0 otherwise
   const int setup_warp = (!CL && !I.state_global) ? 1 : 0;
   if ((tid >> 5) == setup_warp && n_p > 0) {
-    nxt = prefetch_pod(c, I, 0);
+    if (c.pref_regs) nxt = prefetch_pod(c, I, 0);
     pod_setup_warp<B>(s, I, 0, nxt);
   }
   __syncthreads();
