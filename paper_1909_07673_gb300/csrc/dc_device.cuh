@@ -1255,6 +1255,105 @@ static __device__ __forceinline__ void pick_scan(const Sm& s, Lead& me) {
   }
 }
 
+// Paired FP32 arithmetic (two independent lanes per 64-bit register, each
+// rounded like the scalar operation).
+static __device__ __forceinline__ unsigned long long f2_pack(float lo, float hi) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+static __device__ __forceinline__ void f2_unpack(unsigned long long v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+static __device__ __forceinline__ unsigned long long f2_add(unsigned long long a,
+                                                            unsigned long long b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+static __device__ __forceinline__ unsigned long long f2_mul(unsigned long long a,
+                                                            unsigned long long b) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+static __device__ __forceinline__ unsigned long long f2_fma(unsigned long long a,
+                                                            unsigned long long b,
+                                                            unsigned long long c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
+// pick_scan for 6 criteria and TOPSIS, two hosts (u, u + B) per iteration:
+// their FP32 scores are the scalar score32's operation by operation (x - M
+// as x + (-M), exact for integers below 2^24; products, fused squares and the
+// final sum and quotient rounded the same way), computed in paired lanes;
+// the hosts are folded into the Lead in increasing index as in pick_scan.
+template <int B, bool CL>
+static __device__ __forceinline__ void pick_scan_pairs(const Sm& s, Lead& me) {
+  const Ctx& c = *s.c;
+  const int tid = threadIdx.x;
+  const uint32_t tmw = s.tmark[(c.h0 + tid) % B], tyw = s.trymask[(c.h0 + tid) % B];
+  unsigned long long nM[6], nN[6], Q[6];
+#pragma unroll
+  for (int v = 0; v < 6; ++v) {
+    nM[v] = f2_pack(-c.mxf[v], -c.mxf[v]);
+    nN[v] = f2_pack(-c.mnf[v], -c.mnf[v]);
+    Q[v] = f2_pack(c.qf[v], c.qf[v]);
+  }
+  auto fold = [&](int u, float sc, const int32_t* x) {
+    // hosts are visited in increasing index: an equal score keeps the leader
+    if (sc > me.m1) {
+      me.m2 = me.m1;
+      me.m1 = sc;
+      me.idx = u;
+      me.cnt = 1;
+      me.mixed = false;
+#pragma unroll
+      for (int v = 0; v < kMaxC; ++v) me.x[v] = x[v];
+    } else if (sc == me.m1) {
+      if (sc >= 0.f) {
+        me.cnt += 1;
+        me.mixed = me.mixed || !same_vec(x, me.x, 6);
+      }
+    } else {
+      me.m2 = fmaxf(me.m2, sc);
+    }
+  };
+#pragma unroll 1
+  for (int u = c.h0 + tid; u < c.h1; u += 2 * B) {
+    const int u2 = u + B;
+    const bool has2 = u2 < c.h1;
+    const int w2 = has2 ? u2 : u;  // in range; its result is then unused
+    int32_t xa[kMaxC], xb[kMaxC];
+    const int ja = u / B, jb = w2 / B;
+    const bool ispa = (tmw >> ja) & 1u, ispb = (tmw >> jb) & 1u;
+    // host_crit fills the criteria whatever the outcome
+    const bool ca = host_crit<B, 6>(s, u, xa, ispa);
+    const bool cb = host_crit<B, 6>(s, w2, xb, ispb);
+    const bool oka = ca && !((tyw >> ja) & 1u) && commit_possible<B>(s, u, ispa);
+    const bool okb = cb && !((tyw >> jb) & 1u) && commit_possible<B>(s, w2, ispb);
+    unsigned long long dp = 0ull, dn = 0ull;
+#pragma unroll
+    for (int v = 0; v < 6; ++v) {
+      const unsigned long long xv = f2_pack((float)xa[v], (float)xb[v]);
+      const unsigned long long a = f2_mul(f2_add(xv, nM[v]), Q[v]);
+      const unsigned long long b = f2_mul(f2_add(xv, nN[v]), Q[v]);
+      dp = f2_fma(a, a, dp);
+      dn = f2_fma(b, b, dn);
+    }
+    float dpa, dpb, dna, dnb;
+    f2_unpack(dp, dpa, dpb);
+    f2_unpack(dn, dna, dnb);
+    const float sa = __fadd_rn(dpa, dna), sb = __fadd_rn(dpb, dnb);
+    const float sca = sa == 0.f ? 1.f : __fdividef(dna, sa);
+    const float scb = sb == 0.f ? 1.f : __fdividef(dnb, sb);
+    fold(u, oka ? sca : -1.f, xa);
+    if (has2) fold(u2, okb ? scb : -1.f, xb);
+  }
+}
+
 // a5/a6: FP32 scores of every candidate fused with the block argmax, then
 // certification.  Sets c.winner (-1 when no candidate remains) and c.xw, the
 // winner's criteria.  One pass: every thread keeps the Lead of its hosts
@@ -1280,7 +1379,7 @@ static __device__ void pick_host(const Sm& s) {
   // the common configuration (6 criteria, TOPSIS) with both fixed at
   // compile time, every other one with the generic loop
   if (C == 6 && c.method == DC_TOPSIS)
-    pick_scan<B, CL, 6, 1>(s, me);
+    pick_scan_pairs<B, CL>(s, me);
   else
     pick_scan<B, CL, 0, 0>(s, me);
   Lead wl = lead_warp(me, C);
