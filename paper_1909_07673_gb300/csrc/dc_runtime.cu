@@ -154,6 +154,9 @@ struct dc_t {
   int32_t* d_init = nullptr;
   double* d_W = nullptr;
   double* d_L1 = nullptr;
+  // error word of the kernels (a DC_E_* code, 0 when fine): mapped pinned host
+  // memory, so the host reads it after a stream synchronisation without a copy
+  int32_t* h_err = nullptr;
   int32_t* d_err = nullptr;
   // AHP DIFF scratch (one allocation): host list [H], criteria [C][H],
   // inverse column sums [H] (u64), global priorities [H] (f64)
@@ -717,15 +720,18 @@ int dc_create(const dc_config* cfg, void* cuda_stream, dc_t** out) {
       cudaMalloc((void**)&d->d_init, st.size() * 4) != cudaSuccess ||
       cudaMalloc((void**)&d->d_W, kMaxC * sizeof(double)) != cudaSuccess ||
       cudaMalloc((void**)&d->d_L1, kMaxC * sizeof(double)) != cudaSuccess ||
-      cudaMalloc((void**)&d->d_err, sizeof(int32_t)) != cudaSuccess)
+      cudaHostAlloc((void**)&d->h_err, sizeof(int32_t), cudaHostAllocMapped) != cudaSuccess)
     rc = DC_E_NOMEM;
+  if (rc == DC_OK) {
+    *d->h_err = 0;
+    if (cudaHostGetDevicePointer((void**)&d->d_err, d->h_err, 0) != cudaSuccess) rc = DC_E_CUDA;
+  }
   if (rc == DC_OK) {
     double W[kMaxC] = {0};
     for (int v = 0; v < cfg->n_criteria; ++v) W[v] = cfg->weights[v];
     if (cudaMemcpy(d->d_init, st.data(), st.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(d->d_state, st.data(), st.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(d->d_W, W, sizeof(W), cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemset(d->d_err, 0, sizeof(int32_t)) != cudaSuccess)
+        cudaMemcpy(d->d_W, W, sizeof(W), cudaMemcpyHostToDevice) != cudaSuccess)
       rc = DC_E_CUDA;
   }
   if (rc == DC_OK && d->state_global &&
@@ -770,7 +776,7 @@ void dc_destroy(dc_t* d) {
   if (d->d_init) cudaFree(d->d_init);
   if (d->d_W) cudaFree(d->d_W);
   if (d->d_L1) cudaFree(d->d_L1);
-  if (d->d_err) cudaFree(d->d_err);
+  if (d->h_err) cudaFreeHost(d->h_err);
   if (d->d_dx) cudaFree(d->d_dx);
   if (d->d_gstate) cudaFree(d->d_gstate);
   delete d;
@@ -1266,7 +1272,7 @@ int dc_plan_collect(dc_plan* p) {
                      cudaMemcpyDeviceToHost));
   int32_t err = 0;
   for (dc_t* d : p->dcs) {
-    DC_CUDA(cudaMemcpy(&err, d->d_err, sizeof(err), cudaMemcpyDeviceToHost));
+    err = *reinterpret_cast<volatile int32_t*>(d->h_err);
     if (err != 0) return err;
   }
   for (size_t i = 0; i < p->dcs.size(); ++i) {
@@ -1330,8 +1336,8 @@ int dc_schedule(dc_t* const* dcs, int32_t n, int32_t flags) {
     int32_t err = 0;
     for (dc_t* d : p->dcs) {
       if (rc != DC_OK) break;
-      rc = cuda_rc(cudaMemcpy(&err, d->d_err, sizeof(err), cudaMemcpyDeviceToHost));
-      if (rc == DC_OK && err != 0) rc = err;
+      err = *reinterpret_cast<volatile int32_t*>(d->h_err);
+      if (err != 0) rc = err;
     }
   }
   // stream-ordered: the plan's device buffers are released after its work
@@ -1573,6 +1579,7 @@ int dc_rank_hosts(dc_t* d, const dc_request* q, int32_t pod, const int32_t* host
     tmp.d_state = d->d_state;
     tmp.d_L1 = d->d_L1;
     tmp.d_err = d->d_err;
+    tmp.h_err = d->h_err;
     tmp.d_dx = d->d_dx;
     tmp.d_recip = d->d_recip;
     tmp.state_global = d->state_global;
@@ -1609,7 +1616,8 @@ int dc_rank_hosts(dc_t* d, const dc_request* q, int32_t pod, const int32_t* host
   tmp.m_path.release(); tmp.m_status.release(); tmp.m_ndec.release(); tmp.m_score.release();
   tmp.m_tdone.release();
   cudaStreamSynchronize(st);
-  tmp.d_state = nullptr; tmp.d_L1 = nullptr; tmp.d_err = nullptr; tmp.d_dx = nullptr;
+  tmp.d_state = nullptr; tmp.d_L1 = nullptr; tmp.d_err = nullptr; tmp.h_err = nullptr;
+  tmp.d_dx = nullptr;
   tmp.d_gstate = nullptr;
   return rc == DC_OK ? nviable : rc;
 }
