@@ -581,6 +581,17 @@ def serving_child(args):
     return json.loads(r.stdout.strip().splitlines()[-1])["serving"]
 
 
+def optional_section(name, fn, *a):
+    """Runs a section reported beside the main measurement; a failure is
+    reported in that section's key ({"error": ...}, also on stderr) instead of
+    costing the whole JSON line."""
+    try:
+        return fn(*a)
+    except Exception as e:  # noqa: BLE001 - reported, not hidden
+        print("bench: section %s failed: %r" % (name, e), file=sys.stderr, flush=True)
+        return {"error": "%s: %s" % (type(e).__name__, str(e)[-2000:])}
+
+
 def run_ours(args):
     import torch
 
@@ -600,7 +611,8 @@ def run_ours(args):
     # the serving replay first, on an otherwise idle device (rank 0), in a
     # process of its own: run in this process before the autotuner, it left
     # the batched step ~7% slower (measured; each alone did not)
-    serving = None if (args.no_serving or rank != 0) else serving_child(args)
+    serving = None if (args.no_serving or rank != 0) else optional_section(
+        "serving", serving_child, args)
     if dist:
         dist.barrier()
     wl = workload(args, rank)
@@ -705,10 +717,14 @@ def run_ours(args):
     peak, peak_kind = measured_peak()
     achieved = hr * BYTES_PER_HOST_RANKING / (ms_kernel * 1e-3) / 1e9
     traffic = ncu_traffic(hr)
-    largest = None if args.no_largest else run_largest(args, ds, torch, peak)
-    comparators = None if (args.no_comparators or rank != 0) else run_comparators(args, ds, torch)
-    graph = None if (args.no_graph or rank != 0) else run_graph_paths(args, ds, torch, peak)
-    simulation = None if (args.no_simulation or rank != 0) else run_simulation(args, ds, torch)
+    largest = None if args.no_largest else optional_section(
+        "largest_fat_tree", run_largest, args, ds, torch, peak)
+    comparators = None if (args.no_comparators or rank != 0) else optional_section(
+        "comparators", run_comparators, args, ds, torch)
+    graph = None if (args.no_graph or rank != 0) else optional_section(
+        "graph_paths", run_graph_paths, args, ds, torch, peak)
+    simulation = None if (args.no_simulation or rank != 0) else optional_section(
+        "simulation", run_simulation, args, ds, torch)
     if rank != 0:
         if dist:
             dist.barrier()
