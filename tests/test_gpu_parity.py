@@ -76,17 +76,6 @@ def test_k32_single_block(ds, stream):
     check_instance(dc, inst, where="k32")
 
 
-@pytest.mark.parametrize("method,rule", [(W.TOPSIS, W.RATIO), (W.AHP, W.RATIO)])
-def test_k48_global_state(ds, stream, method, rule):
-    """k = 48 (27,648 hosts, the paper-scale fat-tree): the state lives in an
-    L2-resident global copy instead of shared memory.  Pods of 1-8
-    containers, intra-pod links, Pareto bandwidths, 0-100 % pre-load."""
-    inst = W.k48(n_requests=3, method=method, pair_rule=rule).instances[0]
-    dc = ds.load_instance(inst, stream=stream)
-    ds.schedule([dc])
-    check_instance(dc, inst, where="k48/%d" % method)
-
-
 def test_incremental_schedules_and_releases(ds, stream):
     """Submit / schedule / release in several launches; FCFS state carried
     across launches."""
@@ -177,44 +166,48 @@ def test_rank_hosts_scores(ds, stream, method, rule):
             assert np.all(np.isnan(s32[~of])) and np.all(np.isnan(s64[~of]))
 
 
-def test_full_k16_sampled(ds, stream):
-    """The full 1,000-request k=16 workload in the benchmark's launch
-    configuration: every request checked against invariants (capacity never
-    exceeded, conservation, path validity) and the first 150 requests
-    element by element against the oracle."""
+def test_full_k16_whole_chain(ds, stream):
+    """The full 1,000-request k=16 workload (1,024 hosts, 0-70 % pre-load,
+    4-64 containers, 6 criteria, TOPSIS) in one launch: every request and
+    the final state element by element against the oracle."""
     inst = W.k16().instances[0]
     dc = ds.load_instance(inst, stream=stream)
     ds.schedule([dc])
-    ref = check_instance_prefix(dc, inst, 150)
-    H = inst.hosts
-    used_c = np.zeros(H, np.int64)
-    used_m = np.zeros(H, np.int64)
-    used_l = np.zeros(3 * H, np.int64)
-    for r in range(inst.reqs.n):
-        out = dc.query(r)
-        q = inst.reqs.request(r)
-        if out["status"] == ds.ACCEPTED:
-            np.add.at(used_c, out["host"], out["cpu"])
-            np.add.at(used_m, out["host"], out["mem"])
-            assert np.all((out["cpu"] >= q["cpu_min"]) & (out["cpu"] <= q["cpu_max"]))
-            for e in range(len(q["src"])):
-                links = out["path"][6 * e:6 * e + 6]
-                np.add.at(used_l, links[links >= 0], out["bw"][e])
-        else:
-            assert np.all(out["host"] == -1)
-    cap_c = 32 - (inst.pre_cpu.astype(np.int64))
-    cap_m = 64 - (inst.pre_mem.astype(np.int64))
-    assert np.array_equal(dc.state(ds.FREE_CPU), cap_c - used_c)
-    assert np.array_equal(dc.state(ds.FREE_MEM), cap_m - used_m)
-    assert np.array_equal(dc.state(ds.LINK_RES), 10000 - inst.pre_link.astype(np.int64) - used_l)
-    assert np.all(dc.state(ds.LINK_RES) >= 0) and np.all(dc.state(ds.FREE_CPU) >= 0)
+    ref = check_instance(dc, inst, where="k16 full")
+    assert len(ref) == 1000
+    n_acc = sum(r["status"] == O.ACCEPTED for r in ref)
+    assert 0 < n_acc < 1000  # the late requests meet a full data center
 
 
-def check_instance_prefix(dc, inst, n):
-    ref, _ = O.run_instance(inst, max_requests=n)
-    for r in range(n):
-        assert_same_result(dc.query(r), ref[r], "k16 full, req %d" % r)
-    return ref
+@pytest.mark.parametrize("method,rule,n_req", [(W.TOPSIS, W.RATIO, 40), (W.AHP, W.RATIO, 20)])
+def test_k48_chain_launch_shapes(ds, stream, method, rule, n_req):
+    """The paper-scale fat-tree (k = 48, 27,648 hosts, state in L2-resident
+    global memory): the first n_req requests of the 200-request workload
+    (pods of 1-8 containers, Pareto bandwidths, 0-100 % pre-load), one
+    block and thread-block clusters of 4, 8 and 16 blocks of 1024 threads (the shapes the
+    benchmark's autotuner chooses among), every request and the final state
+    element by element against one oracle run."""
+    from parity_util import compare_chain, gpu_results
+
+    inst = W.k48(n_requests=n_req, method=method, pair_rule=rule).instances[0]
+    key = (inst.k, inst.n_criteria, inst.method, inst.pair_rule)
+    runs = []
+    for block, ncta in ((1024, 1), (1024, 16), (1024, 8), (1024, 4)):
+        ds.set_launch(*key, block, ncta)
+        try:
+            dc = ds.load_instance(inst, stream=stream)
+            ds.schedule([dc])
+            runs.append(((block, ncta),) + gpu_results(dc, inst.reqs.n))
+            dc.close()
+        finally:
+            ds.set_launch(*key, 0, 1)
+    ref, odc = O.run_instance(inst)
+    assert sum(r["n_decisions"] for r in ref) > 20 * n_req
+    for shape, got, state in runs:
+        for r in range(len(ref)):
+            assert_same_result(got[r], ref[r], "k48 %s req %d" % (shape, r))
+        for f, g in state.items():
+            assert np.array_equal(g, odc.state(f)), ("k48 state", shape, f)
 
 
 def test_invalid_inputs_rejected(ds, stream):

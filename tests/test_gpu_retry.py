@@ -108,3 +108,30 @@ def test_failures_cluster(ds, stream, ncta):
         check_instance(dc, inst, where="retry cluster %d" % ncta)
     finally:
         ds.set_launch(*key, 0, 1)
+
+
+@pytest.mark.parametrize("method,rule", [(W.TOPSIS, W.RATIO), (W.AHP, W.RATIO), (W.AHP, W.DIFF)])
+@pytest.mark.parametrize("ncta", [1, 2])
+def test_hand_built_retry_order(ds, stream, method, rule, ncta):
+    """The hand-built case of test_oracle_retry.py: the two best-ranked
+    hosts (tied) fail their commit on the second link, the pod lands on host
+    4 (not on its higher-index twin 12, nor on host 2, which a recomputed
+    ranking or an index order would take); with a cluster of two blocks the
+    candidates come from both blocks' host ranges."""
+    from test_oracle_retry import W4, _request, _state
+
+    pc, pm, pl = _state()
+    inst = W.Instance(4, 32, 64, 1000, 4, method, rule, W4, pc, pm, pl,
+                      W.pack_requests([_request(), _request(cpu_pod1=18), _request()]))
+    key = (inst.k, inst.n_criteria, inst.method, inst.pair_rule)
+    if ncta > 1:
+        ds.set_launch(*key, 256, ncta)
+    try:
+        dc = ds.load_instance(inst, stream=stream)
+        ds.schedule([dc])
+        ref = check_instance(dc, inst, where="hand-built retry m%d r%d c%d" % (method, rule, ncta))
+    finally:
+        if ncta > 1:
+            ds.set_launch(*key, 0, 1)
+    assert ref[0]["host"].tolist() == [0, 0, 4]
+    assert ref[1]["status"] == O.REJECTED
