@@ -23,13 +23,22 @@
  *   - int32 arrays are dense and in the caller's index order.
  *   - A dc_t (and every dc_t passed together to one call) is used by one
  *     host thread at a time.
- *   - CUDA errors are reported as DC_E_CUDA; a kernel that reports a bad
- *     input or an exhausted wait returns DC_E_INVAL / DC_E_TIMEOUT and the
- *     instance must be destroyed.
+ *   - CUDA errors are reported as DC_E_CUDA.  The scheduling kernel checks
+ *     that every request fits the scratch memory the launch was given (the
+ *     runtime sizes it, so this only catches a broken invariant); a request
+ *     that does not is left unscheduled (DC_REJECTED, nothing allocated)
+ *     and the call that waits for the launch returns DC_E_INVAL; the
+ *     instance must then be destroyed.  DC_E_TIMEOUT comes from the bounded
+ *     wait of the serving replay (dc_server_set_timeout).
  *
- * Limits (checked, DC_E_INVAL beyond): k even, 2 <= k <= 32 (one thread
- * block holds the whole data center on chip); host_cpu, host_mem <= 65535;
- * link_mbps <= 2^21 - 1; at most 2^18 links per request.
+ * Limits (checked, DC_E_INVAL beyond): k even, 2 <= k <= 48.  Up to k = 32
+ * the scheduling kernel keeps the whole data center (packed host state and
+ * every link residual) in one thread block's shared memory for the whole
+ * launch; above (k = 34..48, up to the 27,648 hosts and 82,944 links of
+ * k = 48) the packed state lives in a per-instance global copy (L2-resident)
+ * and is scheduled by one block of 1024 threads or by a thread-block cluster
+ * (dc_set_launch).  host_cpu, host_mem <= 65535; link_mbps <= 2^21 - 1; per
+ * request at most 2^18 links and c^max <= 65535.
  *
  * Link numbering (also used by dc_query_state and dc_result.path), one
  * undirected residual per link (the u < v storage of Sec. V-D):
@@ -53,7 +62,7 @@ enum {
   DC_E_INVAL = -1,    /* bad argument, bad request, limit exceeded */
   DC_E_NOMEM = -2,    /* host or device allocation failed */
   DC_E_CUDA = -3,     /* a CUDA call failed (sticky per context) */
-  DC_E_TIMEOUT = -4,  /* a bounded device wait ran out */
+  DC_E_TIMEOUT = -4,  /* a bounded wait ran out (dc_server_set_timeout) */
   DC_E_NOTFOUND = -5, /* unknown request id */
   DC_E_BUSY = -6      /* state does not allow the call (e.g. stale plan) */
 };
@@ -129,13 +138,18 @@ typedef struct {
   int64_t done_ns;     /* device clock (ns) when the request finished */
 } dc_result;
 
-/* Creates a data center on the current CUDA device.  cuda_stream: the
- * cudaStream_t (as void*) every operation of this instance is ordered on;
- * NULL = the legacy default stream.  Copies the pre-load arrays.
- * DC_E_INVAL on a bad config or pre-load above capacity. */
+/* Creates a data center G^s(N^s, E^s) (Sec. II-A: servers with capacity
+ * c^s_u[r] for r in {CPU, RAM}, links with bandwidth bw^s_uv; the fat-tree
+ * of Sec. IV-B.1) on the current CUDA device, with the given pre-load
+ * already in use.  cuda_stream: the cudaStream_t (as void*) every operation
+ * of this instance is ordered on; NULL = the legacy default stream.  Copies
+ * the pre-load arrays.  DC_E_INVAL on a bad config or pre-load above
+ * capacity, DC_E_NOMEM when device memory runs out. */
 int dc_create(const dc_config* cfg, void* cuda_stream, dc_t** out);
 
-/* Frees every host and device resource of the instance (waits for its work). */
+/* Frees every host and device resource of the instance (waits for its
+ * work).  No counterpart in the paper (resource management); NULL is a
+ * no-op. */
 void dc_destroy(dc_t* dc);
 
 /* Appends a request to the instance's FCFS queue (Sec. II-A request; FCFS =
@@ -143,35 +157,49 @@ void dc_destroy(dc_t* dc);
  * *req_id receives 0, 1, 2, ... in submission order. */
 int dc_submit_request(dc_t* dc, const dc_request* req, int64_t* req_id);
 
-/* Submits n requests in order (as n calls of dc_submit_request); req_ids[n]
- * may be NULL.  Stops at the first invalid request and returns its error;
+/* Submits n requests in order (as n calls of dc_submit_request: Sec. II-A
+ * requests, FCFS = submission order); req_ids[n] may be NULL.  Stops at the first invalid request and returns its error;
  * the requests before it stay submitted. */
 int dc_submit_batch(dc_t* dc, int32_t n, const dc_request* reqs, int64_t* req_ids);
 
-/* Queues the departure of request req_id after everything submitted so far:
- * when reached, an accepted request returns its CPU, memory and bandwidth
- * (a rejected one returns nothing).  DC_E_NOTFOUND for an unknown id,
- * DC_E_BUSY if it was already queued for release. */
+/* Queues the departure of request req_id after everything submitted so far
+ * (the requests' running times of Sec. IV-B.2 and VI-A: a request leaves
+ * when its duration ends): when reached, an accepted request returns its
+ * CPU, memory and bandwidth (a rejected one returns nothing), and a host
+ * left without containers and pre-load is no longer active (f_u = 0).
+ * DC_E_NOTFOUND for an unknown id, DC_E_BUSY if it was already queued for
+ * release. */
 int dc_release(dc_t* dc, int64_t req_id);
 
-/* Schedules every queued operation of n instances in one batched launch
- * (instances run concurrently; each instance's operations run in FCFS
- * order).  DC_SCHED_SYNC waits for completion; DC_SCHED_ASYNC returns once
- * the work is enqueued (dc_query then reports DC_PENDING until done). */
+/* Schedules every queued operation of n instances in one batched launch:
+ * the greedy heuristic of Sec. V on each instance, first-come first-served
+ * in submission order (pods in index order, each ranked by TOPSIS / AHP over
+ * all hosts, committed on the best host that can carry it, Sec. V-C's
+ * decreasing order on a failed commit, the request rejected and rolled back
+ * when a pod fits nowhere); instances run concurrently.  DC_SCHED_SYNC waits
+ * for completion; DC_SCHED_ASYNC returns once the work is enqueued (dc_query
+ * then reports DC_PENDING until done).  DC_E_INVAL for n <= 0, a NULL or
+ * repeated instance. */
 int dc_schedule(dc_t* const* dcs, int32_t n, int32_t flags);
 
-/* Copies the result of request req_id into caller arrays sized from the
- * request (any output pointer may be NULL).  Waits for an in-flight
+/* Copies the result of request req_id -- the decision (accepted or not)
+ * and the maps M_c (container -> server) and M_ec (link -> path) of Sec.
+ * II-A with the allocations c^a_i, bw^a_ij inside their intervals (Table I)
+ * -- into caller arrays sized from the request (any output pointer may be
+ * NULL).  Waits for an in-flight
  * schedule only if wait != 0; otherwise out->status = DC_PENDING when not
  * finished.  DC_E_NOTFOUND for an unknown id. */
 int dc_query(dc_t* dc, int64_t req_id, dc_result* out, int32_t wait);
 
-/* Copies one state field (see DC_FIELD_*) into out[len]; waits for the
- * instance's queued work first.  DC_E_INVAL if len is too small. */
+/* Copies one field of the data center's state (Sec. II-A: residual server
+ * capacity c^s_u[r], residual link bandwidth bw^s_uv; see DC_FIELD_*) into
+ * out[len]; waits for the instance's queued work first.  DC_E_INVAL for an
+ * unknown field or a len that is too small. */
 int dc_query_state(dc_t* dc, int32_t field, int32_t* out, int64_t len);
 
 /* Ranks every host for pod `pod` of `req` on the current state without
- * committing anything: host_of[n_containers] gives the hosts of containers
+ * committing anything (the per-pod ranking of Sec. V-B / V-C, exposed for
+ * what-if queries): host_of[n_containers] gives the hosts of containers
  * of earlier pods (-1 elsewhere).  Outputs (host arrays, each may be NULL):
  * feasible[H] (0/1), score32[H] (FP32 fast-path score, NaN if not viable),
  * score64[H] (FP64 score with the oracle's arithmetic, NaN if not viable),
@@ -187,7 +215,8 @@ int dc_rank_hosts(dc_t* dc, const dc_request* req, int32_t pod, const int32_t* h
  * of cudaFree).  Same arguments, outputs and return value as dc_rank_hosts.
  * Every device temporary lives in one 1 MiB static device array held by
  * each GPU that loads the library until the process exits; host-side it
- * uses thread-local buffers.  Limits (DC_E_INVAL beyond): at most 1024
+ * uses thread-local buffers (the first call on a host thread may allocate
+ * that thread's copy, about 100 KB).  Limits (DC_E_INVAL beyond): at most 1024
  * containers and 4096 links in `req`, k <= 32.  The first call on a device
  * looks up the array's device address (cudaGetSymbolAddress) with that
  * device current; make that first call before any stream capture.  All
@@ -197,11 +226,14 @@ int dc_rank_hosts(dc_t* dc, const dc_request* req, int32_t pod, const int32_t* h
 int dc_rank_hosts_static(dc_t* dc, const dc_request* req, int32_t pod, const int32_t* host_of,
                          int32_t* feasible, float* score32, double* score64, int32_t* crit);
 
-/* Restores the state given at dc_create and forgets every request. */
+/* Restores the state given at dc_create and forgets every request.  No
+ * counterpart in the paper (replays of one workload). */
 int dc_reset(dc_t* dc);
 
 /* --- plans: the scheduling launch of dc_schedule, prepared once ---------
- * dc_plan_create stages the queued operations of n instances on the device
+ * No counterpart in the paper beyond dc_schedule's (Sec. V) placement, which
+ * a plan runs unchanged; the batching of many requests is the paper's
+ * future work (Sec. VIII).  dc_plan_create stages the queued operations of n instances on the device
  * (request inputs host -> device) and prepares the batched launch; with
  * DC_PLAN_GRAPH it is captured in a CUDA graph; with DC_PLAN_RESET each
  * launch first restores every instance's dc_create state, so the plan can be
@@ -220,7 +252,8 @@ int dc_plan_stats(dc_plan* plan, int64_t* decisions, int64_t* host_rankings,
                   int32_t* kernels_per_launch, int64_t* start_ns);
 
 /* Bytes copied host -> device (request inputs) and device -> host (results)
- * by this instance since dc_create. */
+ * by this instance since dc_create.  No counterpart in the paper
+ * (accounting of the end-to-end measurement). */
 int dc_io_stats(dc_t* dc, int64_t* h2d_bytes, int64_t* d2h_bytes);
 void dc_plan_destroy(dc_plan* plan);
 
@@ -374,13 +407,21 @@ typedef struct {
 
 int dc_server_create(dc_t* const* dcs, int32_t n, int64_t admit_bytes,
                      int32_t max_requests_per_launch, dc_server** out);
+/* Bounded wait of the replay (no counterpart in the paper): a launch whose
+ * data centers report nothing -- no operation completed, no result copy
+ * finished -- for stall_s seconds ends dc_server_replay with DC_E_TIMEOUT
+ * (after the launches in flight have finished; the data centers involved
+ * must then be destroyed).  stall_s = 0 removes the limit; the default is
+ * 30 s.  DC_E_INVAL for a negative or non-finite stall_s. */
+int dc_server_set_timeout(dc_server* srv, double stall_s);
 int dc_server_replay(dc_server* srv, int32_t n_events, const double* t_arrival_s,
                      const int32_t* inst, const int32_t* kind, const dc_request* reqs,
                      const int32_t* release_of, double* latency_s, int64_t* req_id,
                      dc_server_stats* stats);
 void dc_server_destroy(dc_server* srv);
 
-/* Human-readable text of an error code (static storage). */
+/* Human-readable text of an error code (static storage).  No counterpart
+ * in the paper. */
 const char* dc_strerror(int code);
 
 #ifdef __cplusplus

@@ -145,6 +145,10 @@ struct Ctx {
   int32_t pref_regs;  // the next pod's first records are prefetched into registers
                       // (cluster / global state); else an L2 prefetch hint
   int32_t hof_smem;  // hof is this block's shared copy
+  // the request needs more scratch than the launch provides (peer links of
+  // one pod beyond shared memory and the per-block scratch; pods beyond the
+  // decision-record scratch): it is not scheduled and the error word is set
+  int32_t bad_pe, bad_pods;
   Xch xs;
 };
 
@@ -2080,6 +2084,8 @@ static __device__ void load_request(const Sm& s, const InstDev& I, int r, const 
     c.npe = 0;
     c.nfail = 0;
     c.ndec = 0;
+    c.bad_pe = (q.max_pe > kPeS && q.max_pe > I.scr_links) ? 1 : 0;
+    c.bad_pods = q.n_p > I.scr_pods ? 1 : 0;
   }
   if (stage_p)
     for (int i = tid; i <= q.n_p; i += B) {
@@ -2277,6 +2283,20 @@ static __device__ void schedule_request(const Sm& s, const InstDev& I, int r) {
     }
     for (int p = tid; p < n_p; p += B) I.o_score[p_off + p] = -1.0;
   }
+  if (c.bad_pe || c.bad_pods) {
+    // the host runtime sizes the scratch for every queued request, so this
+    // only catches a broken invariant: the request is left unscheduled
+    // (rejected, nothing allocated) and the error word is set (the same
+    // branch in every block of a cluster: the values come from the request)
+    if (tid == 0 && writer) {
+      atomicExch(I.err, DC_E_INVAL);
+      I.o_status[r] = DC_REJECTED;
+      I.o_ndec[r] = 0;
+      I.o_tdone[r] = (long long)globaltimer_ns();
+    }
+    __syncthreads();
+    return;
+  }
   Pre nxt = {make_int4(0, 0, 0, 0), make_int4(0, 0, 0, 0)};
   // the warp that sets up pods (and holds the prefetched records): warp 1 in
   // the one-block shared-memory kernel (it sets up ahead of the commits),
@@ -2444,6 +2464,10 @@ __global__ void __launch_bounds__(B, 1) k_rank(const InstDev* __restrict__ inst,
   const Sm s = carve(smem, I, B);
   load_instance<B, false>(s, I);
   load_request<B>(s, I, r, host_of);
+  if (s.c->bad_pe) {
+    if (threadIdx.x == 0) atomicExch(I.err, DC_E_INVAL);
+    return;
+  }
   if (s.c->hof != s.st_hof) {
     // request too large to stage: the global host_of is read directly
     if (threadIdx.x == 0) s.c->hof = const_cast<int32_t*>(host_of);

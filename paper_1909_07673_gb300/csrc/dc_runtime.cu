@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstdlib>
@@ -1598,6 +1599,7 @@ int dc_rank_hosts(dc_t* d, const dc_request* q, int32_t pod, const int32_t* host
     if (rc == DC_OK && score64) rc = cuda_rc(cudaMemcpy(score64, d_s64, H * 8, cudaMemcpyDeviceToHost));
     if (rc == DC_OK && crit) rc = cuda_rc(cudaMemcpy(crit, d_crit, (size_t)H * C * 4, cudaMemcpyDeviceToHost));
     if (rc == DC_OK) rc = cuda_rc(cudaMemcpy(&nviable, d_nv, 4, cudaMemcpyDeviceToHost));
+    if (rc == DC_OK) rc = *reinterpret_cast<volatile int32_t*>(d->h_err);
   }
   cudaFree(d_host_of); cudaFree(d_feas); cudaFree(d_crit); cudaFree(d_nv);
   cudaFree(d_s32); cudaFree(d_s64); cudaFree(d_desc);
@@ -1673,20 +1675,24 @@ static_assert(static_layout().total <= kStaticScratchBytes, "static scratch too 
 __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
 // Device address of g_static_scratch per device (the host-side name is only a
-// stand-in for the symbol, never a device address).
+// stand-in for the symbol, never a device address).  Host threads may make
+// their first call on a device at the same time: both look the address up
+// (the same value) and store it atomically.
 constexpr int kMaxDevices = 64;
-unsigned char* g_static_ptr[kMaxDevices] = {nullptr};
+std::atomic<unsigned char*> g_static_ptr[kMaxDevices] = {};
 
 int static_scratch(unsigned char** out) {
   int dev = 0;
   DC_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= kMaxDevices) return DC_E_INVAL;
-  if (!g_static_ptr[dev]) {
-    void* p = nullptr;
-    DC_CUDA(cudaGetSymbolAddress(&p, g_static_scratch));
-    g_static_ptr[dev] = static_cast<unsigned char*>(p);
+  unsigned char* p = g_static_ptr[dev].load(std::memory_order_acquire);
+  if (!p) {
+    void* a = nullptr;
+    DC_CUDA(cudaGetSymbolAddress(&a, g_static_scratch));
+    p = static_cast<unsigned char*>(a);
+    g_static_ptr[dev].store(p, std::memory_order_release);
   }
-  *out = g_static_ptr[dev];
+  *out = p;
   return DC_OK;
 }
 
@@ -1779,17 +1785,9 @@ extern "C" int dc_rank_hosts_static(dc_t* d, const dc_request* q, int32_t pod,
   unsigned char* base = nullptr;
   DC_TRY(static_scratch(&base));
   constexpr StaticLayout L = static_layout();
-  InstDev I{};
-  I.k = d->k; I.half = d->half; I.H = d->H; I.E = d->E;
-  I.C = d->cfg.n_criteria; I.method = d->cfg.method; I.rule = d->cfg.pair_rule;
-  I.host_cpu = d->cfg.host_cpu; I.host_mem = d->cfg.host_mem; I.link_mbps = d->cfg.link_mbps;
-  for (int v = 0; v < kMaxC; ++v) I.W[v] = v < I.C ? d->cfg.weights[v] : 0.0;
-  I.L1 = d->d_L1;
-  I.cpu = d->d_state;
-  I.mem = d->d_state + d->H;
-  I.ctr = d->d_state + 2 * d->H;
-  I.pre = d->d_state + 3 * d->H;
-  I.res = d->d_state + 4 * d->H;
+  // the instance's descriptor (state, criteria weights, AHP scratch, error
+  // word), with the request, host map and scratch moved to the static array
+  InstDev I = make_desc(d, nullptr, 0, nullptr);
   I.reqs = reinterpret_cast<const ReqRec*>(base + L.req);
   I.c_lay = reinterpret_cast<const int4*>(base + L.c_lay);
   I.e_lay = reinterpret_cast<const int4*>(base + L.e_lay);
@@ -1800,17 +1798,8 @@ extern "C" int dc_rank_hosts_static(dc_t* d, const dc_request* q, int32_t pod,
   I.scr_pods = 1;
   I.scr_pe = reinterpret_cast<int4*>(base + L.pel);
   I.scr_log = reinterpret_cast<PodLog*>(base + L.log);
-  I.err = d->d_err;
-  if (d->d_dx) {  // the instance's own AHP DIFF scratch (allocated by dc_create)
-    const size_t Hh = (size_t)d->H;
-    I.dx_idx = reinterpret_cast<int32_t*>(d->d_dx);
-    I.dx_val = reinterpret_cast<int32_t*>(d->d_dx + 4 * Hh);
-    I.dx_inv = reinterpret_cast<unsigned long long*>(d->d_dx + 4 * Hh * (1 + kMaxC));
-    I.dx_pg = reinterpret_cast<double*>(d->d_dx + 4 * Hh * (1 + kMaxC) + 8 * Hh);
-  }
-  I.recip = d->d_recip;
-  I.state_global = d->state_global ? 1 : 0;
-  I.gstate = d->d_gstate;
+  I.progress = nullptr;
+  I.counters = nullptr;
   cudaStream_t st = d->stream;
   const int32_t n = rec.n_c, m = rec.n_e, P = rec.n_p, H = d->H, C = d->cfg.n_criteria;
   DC_CUDA(cudaMemcpyAsync(base + L.desc, &I, sizeof(I), cudaMemcpyHostToDevice, st));
@@ -1832,7 +1821,8 @@ extern "C" int dc_rank_hosts_static(dc_t* d, const dc_request* q, int32_t pod,
   if (crit) DC_CUDA(cudaMemcpyAsync(crit, base + L.crit, (size_t)H * C * 4, cudaMemcpyDeviceToHost, st));
   DC_CUDA(cudaMemcpyAsync(&nviable, base + L.nv, 4, cudaMemcpyDeviceToHost, st));
   DC_CUDA(cudaStreamSynchronize(st));
-  return nviable;
+  const int32_t err = *reinterpret_cast<volatile int32_t*>(d->h_err);
+  return err != 0 ? err : nviable;
 }
 
 // ---------------------------------------------------------------------------
@@ -1856,6 +1846,9 @@ struct dc_server {
   int32_t* h_prog = nullptr;  // [n] host-mapped progress words
   int32_t* d_prog = nullptr;
   std::vector<cudaStream_t> pool;  // launch streams (one per running launch)
+  // a launch that shows no progress for this long ends the replay with
+  // DC_E_TIMEOUT (0: no limit)
+  double stall_s = 30.0;
 };
 
 namespace {
@@ -1878,6 +1871,7 @@ struct Flight {
   std::vector<cudaEvent_t> collect_ev;      // per plan dc: results copied
   std::vector<char> retired;                // per plan dc: released to the loop
   int32_t live = 0;                         // plan dcs not retired yet
+  double t_progress = 0.0;                  // replay clock at its last progress
 };
 
 }  // namespace
@@ -1949,6 +1943,12 @@ int server_stream(dc_server* s, std::vector<char>& used) {
   return (int)s->pool.size() - 1;
 }
 }  // namespace
+
+extern "C" int dc_server_set_timeout(dc_server* s, double stall_s) {
+  if (!s || !(stall_s >= 0.0) || !std::isfinite(stall_s)) return DC_E_INVAL;
+  s->stall_s = stall_s;
+  return DC_OK;
+}
 
 extern "C" void dc_server_destroy(dc_server* s) {
   if (!s) return;
@@ -2064,6 +2064,7 @@ extern "C" int dc_server_replay(dc_server* s, int32_t n_ev, const double* t_arr,
             if (kind[e] == 0) latency[e] = t - t_arr[e];
           }
           progress = true;
+          fl.t_progress = t;
         }
         if (cnt == nops + 1 && !fl.collect_ev[j]) {
           dc_t* d = p->dcs[j];
@@ -2071,6 +2072,7 @@ extern "C" int dc_server_replay(dc_server* s, int32_t n_ev, const double* t_arr,
           if (rc == DC_OK) rc = cuda_rc(cudaEventCreateWithFlags(&fl.collect_ev[j], cudaEventDisableTiming));
           if (rc == DC_OK) rc = cuda_rc(cudaEventRecord(fl.collect_ev[j], d->stream));
           progress = true;
+          fl.t_progress = elapsed();
         }
         if (rc == DC_OK && fl.collect_ev[j]) {
           const cudaError_t q = cudaEventQuery(fl.collect_ev[j]);
@@ -2097,8 +2099,13 @@ extern "C" int dc_server_replay(dc_server* s, int32_t n_ev, const double* t_arr,
           busy[i] = 0;
           fl.live -= 1;
           progress = true;
+          fl.t_progress = elapsed();
         }
       }
+      // bounded wait: a launch whose data centers report nothing (no
+      // operation done, no result copy finished) for stall_s seconds
+      if (rc == DC_OK && s->stall_s > 0.0 && fl.live > 0 && elapsed() - fl.t_progress > s->stall_s)
+        rc = DC_E_TIMEOUT;
       if (rc == DC_OK && fl.live == 0 && cudaEventQuery(p->done_ev) == cudaSuccess) {
         stream_used[fl.stream_slot] = 0;
         destroy_plan_resources(p);
@@ -2146,6 +2153,7 @@ extern "C" int dc_server_replay(dc_server* s, int32_t n_ev, const double* t_arr,
         fl.collect_ev.assign(group.size(), nullptr);
         fl.retired.assign(group.size(), 0);
         fl.live = (int32_t)group.size();
+        fl.t_progress = elapsed();
         for (int32_t i : group) busy[i] = 1;
         flights.push_back(std::move(fl));
         ++st.launches;

@@ -21,6 +21,7 @@ PENDING, ACCEPTED, REJECTED = 0, 1, 2
 SCHED_SYNC, SCHED_ASYNC = 0, 1
 PLAN_GRAPH, PLAN_RESET = 1, 2
 FREE_CPU, FREE_MEM, CTR, PRE, LINK_RES = 0, 1, 2, 3, 4
+E_INVAL, E_NOMEM, E_CUDA, E_TIMEOUT, E_NOTFOUND, E_BUSY = -1, -2, -3, -4, -5, -6
 
 _i32p = C.POINTER(C.c_int32)
 _i64p = C.POINTER(C.c_int64)
@@ -100,6 +101,7 @@ def lib():
         L.dc_server_replay.argtypes = [C.c_void_p, C.c_int32, _f64p, _i32p, _i32p,
                                        C.POINTER(_Request), _i32p, _f64p, _i64p,
                                        C.POINTER(_ServerStats)]
+        L.dc_server_set_timeout.argtypes = [C.c_void_p, C.c_double]
         L.dc_server_destroy.argtypes = [C.c_void_p]
         L.dc_server_destroy.restype = None
         L.dc_plan_create.argtypes = [C.POINTER(C.c_void_p), C.c_int32, C.c_int32,
@@ -356,12 +358,14 @@ class Server:
     """Continuous-batching serving loop over resident data centers (dc_server)."""
 
     def __init__(self, dcs: Sequence[DataCenter], admit_bytes: int = 1 << 30,
-                 max_requests_per_launch: int = 0):
+                 max_requests_per_launch: int = 0, stall_s: Optional[float] = None):
         self.dcs = list(dcs)
         h = C.c_void_p()
         _check(lib().dc_server_create(_handles(self.dcs), len(self.dcs), admit_bytes,
                                       max_requests_per_launch, C.byref(h)), "dc_server_create")
         self.h = h
+        if stall_s is not None:
+            _check(lib().dc_server_set_timeout(h, stall_s), "dc_server_set_timeout")
 
     def replay(self, t, inst, kind, reqs, release_of):
         """Replays timed events (see dc_server_replay); reqs[i] is a request

@@ -30,6 +30,8 @@ def test_binding_constants_match_header():
         "DC_PLAN_GRAPH": ds.PLAN_GRAPH, "DC_PLAN_RESET": ds.PLAN_RESET,
         "DC_FIELD_FREE_CPU": ds.FREE_CPU, "DC_FIELD_FREE_MEM": ds.FREE_MEM,
         "DC_FIELD_CTR": ds.CTR, "DC_FIELD_PRE": ds.PRE, "DC_FIELD_LINK_RES": ds.LINK_RES,
+        "DC_E_INVAL": ds.E_INVAL, "DC_E_NOMEM": ds.E_NOMEM, "DC_E_CUDA": ds.E_CUDA,
+        "DC_E_TIMEOUT": ds.E_TIMEOUT, "DC_E_NOTFOUND": ds.E_NOTFOUND, "DC_E_BUSY": ds.E_BUSY,
     }
     for name, value in pairs.items():
         assert name in h, name

@@ -58,3 +58,39 @@ def test_served_results_equal_oracle_and_alone(max_per_launch, admit_bytes):
         alone.close()
     for d in dcs:
         d.close()
+
+
+def test_replay_stall_returns_timeout():
+    """The replay's bounded wait: one request of 60,000 zero-size singleton
+    pods on a k=16 data center is a single operation of ~0.7 s on the device
+    (a pod decision is ~11 us), during which the kernel reports no progress;
+    with a 0.1 s stall limit the replay returns DC_E_TIMEOUT once the launch
+    has finished, and the library keeps working afterwards."""
+    import torch
+    from paper_1909_07673_gb300 import dcsched as ds
+
+    torch.cuda.set_device(0)
+    n = 60000
+    z = np.zeros(n, np.int32)
+    e = np.zeros(0, np.int32)
+    big = {"cpu_min": z, "cpu_max": z, "mem_min": z, "mem_max": z,
+           "pod": np.arange(n, dtype=np.int32), "src": e, "dst": e, "bw_min": e, "bw_max": e}
+    dc = ds.DataCenter(16, 32, 64, 10000, 6, ds.TOPSIS, ds.RATIO, (1 / 6,) * 6,
+                       stream=torch.cuda.Stream())
+    srv = ds.Server([dc], stall_s=0.1)
+    with pytest.raises(ds.DcError) as ei:
+        srv.replay(np.zeros(1), np.zeros(1, np.int32), np.zeros(1, np.int32), [big],
+                   np.zeros(1, np.int32))
+    assert ei.value.code == ds.E_TIMEOUT
+    srv.close()
+    dc.close()
+    with pytest.raises(ds.DcError):
+        ds.Server([], stall_s=1.0)
+    # a fresh data center schedules normally after the timeout
+    inst = W.small().instances[0]
+    fresh = ds.load_instance(inst, stream=torch.cuda.Stream())
+    ds.schedule([fresh])
+    ref, _ = O.run_instance(inst)
+    for r in range(inst.reqs.n):
+        assert_same_result(fresh.query(r), ref[r], "after timeout req %d" % r)
+    fresh.close()
