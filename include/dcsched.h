@@ -339,7 +339,7 @@ int dc_graph_widest_paths(dc_graph* g, int32_t n_pairs, const int32_t* src, cons
  * created afterwards (dc_plan_create, dc_schedule, servers) use it.  The
  * table is process-wide; without an entry a data center keeps the shape
  * dc_create chose.  block: 128, 256, 512 or 1024 with k^3/4 <= 32 * block;
- * ncta: 1, or 2..16 dividing k with block >= 256 and not AHP DIFF.
+ * ncta: 1, or 2..16 dividing k with block >= 256.
  * block = 0 removes the entry.  DC_E_INVAL for a shape that cannot run such
  * a data center on the current device (shared memory, cluster residency).
  * dc_get_launch reports the shape a plan created now would use for dc. */

@@ -75,6 +75,7 @@ struct Xch {
   int32_t idx64;
   int32_t x64[kMaxC];
   int32_t ok;                      // commit result (rank 0)
+  unsigned long long dsum[4];      // AHP DIFF: block totals of a cluster scan
 };
 
 struct Ctx {
@@ -129,7 +130,10 @@ struct Ctx {
   int32_t commit_ok;
   int32_t arrive;
   int32_t ndec;
-  int32_t nvc;      // viable hosts counted by the AHP DIFF compaction
+  // AHP DIFF: distinct values of each criterion among the viable hosts,
+  // and this block's exclusive offset / the cluster's totals of a scan
+  int32_t dD[kMaxC];
+  unsigned long long doff[4], dtot[4];
   double wscore;    // AHP DIFF: exact global priority of the winner
   int32_t cnt1;     // hosts at the maximum FP32 score
   int32_t mixed;    // some host at the maximum has other criteria than idx1
@@ -1026,18 +1030,8 @@ static __device__ void column_fp64(const Sm& s) {
 }
 
 // ------------------------------------------------------------- AHP DIFF
-//
-// Local priorities under the difference rule (Sec. V-B), exactly as the
-// oracle defines them: for criterion v over the F viable hosts,
-//   A(d) = d * 2^64 (d > 0), 2^64 (d = 0 or -1), round(2^64 / -d) (d < -1),
-//   S_j = sum_i A(x_i - x_j),  I_j = rint(2^64 / double(S_j * 2^-64)),
-//   term(d, I) = q * I for an integer entry q (d >= -1, q = max(d, 1)),
-//                floor((round(2^64 / -d) * I + 2^63) / 2^64) otherwise,
-//   L2_i = (double(sum_j term(x_i - x_j, I_j)) * 2^-64) / F,
-// sums exact in unsigned 128-bit integers (order-free), every floating-point
-// step one IEEE binary64 operation rounded to nearest.  F = 1 gives L2 = 1.
-// The global priority PG = sum_v L1_v * L2_v is then an exact FP64 value, so
-// the selection needs no guard band.  Cost O(F^2) per criterion.
+// 128-bit fixed-point helpers of the difference rule (the rule itself is
+// further down, after the selection helpers).
 
 static __device__ __forceinline__ unsigned long long recip_long(unsigned long long m) {
   // floor((2^65 + m) / (2m)) by long division over 32-bit limbs, m < 2^31
@@ -1071,68 +1065,6 @@ static __device__ __forceinline__ void add128(unsigned long long& lo, unsigned l
                                               unsigned long long alo, unsigned long long ahi) {
   lo += alo;
   hi += ahi + (lo < alo ? 1ull : 0ull);
-}
-
-// Compacts the viable hosts with their criteria, then computes the global
-// priority of each into I.dx_pg (block-wide; ends with a barrier).
-template <int B>
-static __device__ void diff_scores(const Sm& s, const InstDev& I) {
-  Ctx& c = *s.c;
-  const int tid = threadIdx.x, H = c.H, C = c.C;
-  if (tid == 0) c.nvc = 0;
-  __syncthreads();
-  for (int u = tid; u < H; u += B) {
-    int32_t x[kMaxC];
-    if (host_crit<B>(s, u, x)) {
-      const int p = atomicAdd(&c.nvc, 1);
-      I.dx_idx[p] = u;
-      for (int v = 0; v < C; ++v) I.dx_val[v * H + p] = x[v];
-    }
-  }
-  __syncthreads();
-  const int F = c.nvc;
-  for (int v = 0; v < C; ++v) {
-    const int32_t* X = I.dx_val + v * H;
-    if (F > 1) {
-      for (int p = tid; p < F; p += B) {
-        const int xp = X[p];
-        unsigned long long lo = 0, hi = 0;
-        for (int q = 0; q < F; ++q) {
-          const int d = X[q] - xp;
-          if (d > 0) add128(lo, hi, 0ull, (unsigned long long)d);
-          else if (d >= -1) add128(lo, hi, 0ull, 1ull);
-          else add128(lo, hi, recip_q64(I.recip, -d), 0ull);
-        }
-        const double sj = __dmul_rn(u128_to_double(lo, hi), 0x1p-64);
-        const double inv = __ddiv_rn(1.0, sj);
-        I.dx_inv[p] = __double2ull_rn(__dmul_rn(inv, 0x1p64));
-      }
-      __syncthreads();
-    }
-    for (int p = tid; p < F; p += B) {
-      double l2 = 1.0;
-      if (F > 1) {
-        const int xp = X[p];
-        unsigned long long lo = 0, hi = 0;
-        for (int q = 0; q < F; ++q) {
-          const int d = xp - X[q];
-          const unsigned long long Iq = I.dx_inv[q];
-          if (d >= -1) {
-            const unsigned long long qq = d > 0 ? (unsigned long long)d : 1ull;
-            add128(lo, hi, qq * Iq, __umul64hi(qq, Iq));
-          } else {
-            const unsigned long long R = recip_q64(I.recip, -d);
-            const unsigned long long plo = R * Iq, phi = __umul64hi(R, Iq);
-            add128(lo, hi, phi + (plo >> 63), 0ull);
-          }
-        }
-        l2 = __ddiv_rn(__dmul_rn(u128_to_double(lo, hi), 0x1p-64), (double)F);
-      }
-      const double pg = v == 0 ? 0.0 : I.dx_pg[p];
-      I.dx_pg[p] = __dadd_rn(pg, __dmul_rn(c.L1[v], l2));
-    }
-    __syncthreads();
-  }
 }
 
 // block-wide (max, lowest index, number of hosts at the max, second
@@ -1656,19 +1588,514 @@ static __device__ void pick_fit(const Sm& s) {
   __syncthreads();
 }
 
-// a6 under AHP DIFF: exact FP64 argmax (lowest index on ties) over the viable
-// hosts whose commit can succeed and that did not fail one.
+// ------------------------------------------------------------- AHP DIFF
+//
+// Local priorities under the difference rule (Sec. V-B, Eqs. 9-10), exactly
+// as the oracle defines them: for criterion v over the F viable hosts,
+//   A(d) = d * 2^64 (d > 0), 2^64 (d = 0 or -1), R(-d) (d < -1),
+//   R(m) = round(2^64 / m),
+//   S_j = sum_i A(x_i - x_j),  I_j = rint(2^64 / double(S_j * 2^-64)),
+//   term(d, I) = max(d, 1) * I (d >= -1),
+//                floor((R(-d) * I + 2^63) / 2^64) (d < -1),
+//   L2_i = (double(sum_j term(x_i - x_j, I_j)) * 2^-64) / F   (F = 1: 1),
+// sums exact in unsigned 128-bit integers.  Hosts with equal values have
+// equal sums, so everything is evaluated over the D distinct values y_0 <
+// ... < y_{D-1} of the viable hosts with their counts n_j, and the parts of
+// the sums that are linear in the value come from prefix sums:
+//   S_j = 2^64 [sum_{i>j} n_i (y_i - y_j) + n_j + n(y_j - 1)]
+//         + sum_{y_i <= y_j - 2} n_i R(y_j - y_i)
+//   T_i = y_i P1_i - P2_i + n_i I_i + n(y_i + 1) I(y_i + 1)
+//         + sum_{y_j >= y_i + 2} n_j floor((R(y_j - y_i) I_j + 2^63) / 2^64)
+// with P1_i = sum_{j<i} n_j I_j and P2_i = sum_{j<i} n_j y_j I_j; these are
+// the same integers as the oracle's sums over all pairs, so the priorities
+// are bit-identical.  Only the pairs at least two values apart are
+// evaluated one by one: D (D - 1) / 2 pairs for the column sums and as many
+// for the row sums, per criterion and decision, one warp per distinct
+// value.  The global priority PG = sum_v L1_v L2_v is the exact FP64 value
+// of the oracle, so the selection needs no guard band.
+//
+// Phases of one decision (every block of a cluster takes every branch: the
+// values that steer them are combined exactly):
+//   hist     criteria of this block's hosts, one histogram per criterion
+//            over the values (warp-aggregated global atomics)
+//   compact  per criterion, the non-empty bins in value order become the
+//            distinct list with inclusive prefix sums of n and n * y (a
+//            block scan, the block offsets combined through distributed
+//            shared memory); each bin then holds its value's index
+//   columns  S_j and I_j, one warp per distinct value over all criteria
+//   prefix   per criterion, exclusive 128-bit prefix sums of n_j I_j and
+//            n_j y_j I_j (block scan + cluster offsets)
+//   rows     T_i and L2_i, one warp per distinct value
+//   priority PG of this block's viable hosts (-1 for the others); then the
+//            used bins are cleared for the next decision
+
+typedef unsigned long long u64;
+
+// barrier of the data center's blocks (the block; with a cluster, the
+// cluster barrier with release / acquire of global and shared memory)
+template <bool CL>
+static __device__ __forceinline__ void dc_sync() {
+  if (CL) cl_sync();
+  else __syncthreads();
+}
+
+// 128-bit helpers: shuffles and products
+static __device__ __forceinline__ void shfl_up128(u64& lo, u64& hi, int o) {
+  lo = __shfl_up_sync(0xffffffffu, lo, o);
+  hi = __shfl_up_sync(0xffffffffu, hi, o);
+}
+static __device__ __forceinline__ void warp_sum128(u64& lo, u64& hi) {
+  for (int o = 16; o > 0; o >>= 1) {
+    const u64 a = __shfl_xor_sync(0xffffffffu, lo, o), b = __shfl_xor_sync(0xffffffffu, hi, o);
+    add128(lo, hi, a, b);
+  }
+}
+// (hi:lo) * m for m < 2^32, modulo 2^128
+static __device__ __forceinline__ void mul128_32(u64& lo, u64& hi, u64 m) {
+  const u64 plo = lo * m, carry = __umul64hi(lo, m);
+  hi = hi * m + carry;
+  lo = plo;
+}
+static __device__ __forceinline__ void sub128(u64& lo, u64& hi, u64 blo, u64 bhi) {
+  const u64 borrow = lo < blo ? 1ull : 0ull;
+  lo -= blo;
+  hi -= bhi + borrow;
+}
+
+// Block-wide exclusive scan of four 64-bit words per thread in thread
+// order, added as two 128-bit numbers (w[0], w[1]) and (w[2], w[3]) when
+// WIDE, else as four independent 64-bit sums.  ex receives the thread's
+// exclusive prefix, tot the block total (every thread).  Uses s.red64
+// ([B / 32][4]) and ends with a barrier.
+template <int B, bool WIDE>
+static __device__ void block_scan4(const Sm& s, const u64* w, u64* ex, u64* tot) {
+  constexpr int NW = B / 32;
+  const int lane = lane_id(), wp = threadIdx.x >> 5;
+  u64 in[4] = {w[0], w[1], w[2], w[3]};
+  // warp inclusive scan
+  for (int o = 1; o < 32; o <<= 1) {
+    u64 t[4] = {in[0], in[1], in[2], in[3]};
+    if (WIDE) {
+      shfl_up128(t[0], t[1], o);
+      shfl_up128(t[2], t[3], o);
+      if (lane >= o) {
+        add128(in[0], in[1], t[0], t[1]);
+        add128(in[2], in[3], t[2], t[3]);
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        t[q] = __shfl_up_sync(0xffffffffu, t[q], o);
+        if (lane >= o) in[q] += t[q];
+      }
+    }
+  }
+  u64* wt = reinterpret_cast<u64*>(s.red64);
+  if (lane == 31)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) wt[wp * 4 + q] = in[q];
+  __syncthreads();
+  // warp 0 turns the warp totals into exclusive warp offsets (in place)
+  if (wp == 0) {
+    u64 t[4] = {0, 0, 0, 0};
+    if (lane < NW)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) t[q] = wt[lane * 4 + q];
+    u64 acc[4] = {t[0], t[1], t[2], t[3]};
+    for (int o = 1; o < 32; o <<= 1) {
+      u64 y[4] = {acc[0], acc[1], acc[2], acc[3]};
+      if (WIDE) {
+        shfl_up128(y[0], y[1], o);
+        shfl_up128(y[2], y[3], o);
+        if (lane >= o) {
+          add128(acc[0], acc[1], y[0], y[1]);
+          add128(acc[2], acc[3], y[2], y[3]);
+        }
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          y[q] = __shfl_up_sync(0xffffffffu, y[q], o);
+          if (lane >= o) acc[q] += y[q];
+        }
+      }
+    }
+    // the block total sits in lane NW - 1
+    u64 T[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) T[q] = __shfl_sync(0xffffffffu, acc[q], NW - 1);
+    if (lane < NW) {
+      // exclusive = inclusive - own
+      if (WIDE) {
+        sub128(acc[0], acc[1], t[0], t[1]);
+        sub128(acc[2], acc[3], t[2], t[3]);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] -= t[q];
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) wt[lane * 4 + q] = acc[q];
+    }
+    if (lane < 4) wt[NW * 4 + lane] = T[lane];
+  }
+  __syncthreads();
+  // the thread's exclusive prefix: warp offset + inclusive - own
+  u64 e[4] = {wt[wp * 4 + 0], wt[wp * 4 + 1], wt[wp * 4 + 2], wt[wp * 4 + 3]};
+  u64 own[4] = {w[0], w[1], w[2], w[3]};
+  if (WIDE) {
+    sub128(in[0], in[1], own[0], own[1]);
+    sub128(in[2], in[3], own[2], own[3]);
+    add128(e[0], e[1], in[0], in[1]);
+    add128(e[2], e[3], in[2], in[3]);
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) e[q] += in[q] - own[q];
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    ex[q] = e[q];
+    tot[q] = wt[NW * 4 + q];
+  }
+  __syncthreads();
+}
+
+// This block's offset and the data center's total of per-block values
+// (four words, 128-bit pairs when WIDE) into c.doff / c.dtot: each block
+// publishes its total, and after a barrier of the data center's blocks
+// thread 0 adds up the totals of the lower ranks (distributed shared
+// memory) and of all ranks.  Ends with a block barrier.
+template <bool CL, bool WIDE>
+static __device__ void cluster_offsets(const Sm& s, const u64* tot) {
+  Ctx& c = *s.c;
+  if (CL) {
+    if (threadIdx.x == 0)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) c.xs.dsum[q] = tot[q];
+    cl_sync();
+    if (threadIdx.x == 0) {
+      u64 off[4] = {0, 0, 0, 0}, all[4] = {0, 0, 0, 0};
+      for (int r = 0; r < c.ncta; ++r) {
+        const Xch* R = cl_map(&c.xs, r);
+        u64 v[4] = {R->dsum[0], R->dsum[1], R->dsum[2], R->dsum[3]};
+        if (WIDE) {
+          if (r < c.rank) {
+            add128(off[0], off[1], v[0], v[1]);
+            add128(off[2], off[3], v[2], v[3]);
+          }
+          add128(all[0], all[1], v[0], v[1]);
+          add128(all[2], all[3], v[2], v[3]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            if (r < c.rank) off[q] += v[q];
+            all[q] += v[q];
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        c.doff[q] = off[q];
+        c.dtot[q] = all[q];
+      }
+    }
+  } else if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      c.doff[q] = 0;
+      c.dtot[q] = tot[q];
+    }
+  }
+  __syncthreads();
+}
+
+// hist: criteria of this block's hosts into dx_x (criterion 0 = -1 for a
+// host that is not viable) and the viable hosts' values into one histogram
+// per criterion; lanes with equal values add them with one atomic.
 template <int B>
+static __device__ void diff_hist(const Sm& s, const InstDev& I) {
+  const Ctx& c = *s.c;
+  const int C = c.C, H = c.H, lane = lane_id();
+  for (int ub = c.h0 + (int)(threadIdx.x & ~31u); ub < c.h1; ub += B) {
+    const int u = ub + lane;
+    int32_t x[kMaxC];
+    bool f = false;
+    if (u < c.h1) {
+      f = host_crit<B>(s, u, x);
+      I.dx_x[u] = f ? x[0] : -1;
+      for (int v = 1; v < C; ++v) I.dx_x[v * H + u] = x[v];
+    }
+    for (int v = 0; v < C; ++v) {
+      const int key = f ? x[v] : -1;
+      const unsigned peers = __match_any_sync(0xffffffffu, key);
+      if (f && lane == __ffs(peers) - 1) atomicAdd(&I.dx_hist[I.dx_hoff[v] + key], __popc(peers));
+    }
+  }
+}
+
+// compact, criterion v: the bins [mn_v, mx_v] are split between the blocks
+// (block r the r-th slice) and inside a block between the threads
+// (contiguous chunks), so that thread order is value order.  Writes the
+// distinct list dx_vn[v] (value, count) with the inclusive prefix sums
+// dx_py[v] (count, count * value), replaces each non-empty bin by its index
+// and sets c.dD[v].  Ends with a barrier of the data center's blocks.
+template <int B, bool CL>
+static __device__ void diff_compact(const Sm& s, const InstDev& I, int v) {
+  Ctx& c = *s.c;
+  const int H = c.H, tid = threadIdx.x;
+  int32_t* hist = I.dx_hist + I.dx_hoff[v];
+  const long long lo = c.mn[v], R = (long long)c.mx[v] - c.mn[v] + 1;
+  const int b0 = (int)(lo + R * c.rank / c.ncta), b1 = (int)(lo + R * (c.rank + 1) / c.ncta);
+  const long long nb = b1 - b0;
+  const int t0 = b0 + (int)(nb * tid / B), t1 = b0 + (int)(nb * (tid + 1) / B);
+  u64 w[4] = {0, 0, 0, 0};  // distinct values, hosts, sum of values, unused
+  for (int y = t0; y < t1; ++y) {
+    const int n = hist[y];
+    if (n) {
+      w[0] += 1;
+      w[1] += (u64)n;
+      w[2] += (u64)n * (u64)y;
+    }
+  }
+  u64 ex[4], tot[4];
+  block_scan4<B, false>(s, w, ex, tot);
+  cluster_offsets<CL, false>(s, tot);
+  if (tid == 0) c.dD[v] = (int32_t)c.dtot[0];
+  int2* vn = I.dx_vn + (size_t)v * H;
+  longlong2* py = I.dx_py + (size_t)v * H;
+  long long k = (long long)(c.doff[0] + ex[0]);
+  long long pn = (long long)(c.doff[1] + ex[1]), pyv = (long long)(c.doff[2] + ex[2]);
+  for (int y = t0; y < t1; ++y) {
+    const int n = hist[y];
+    if (n) {
+      pn += n;
+      pyv += (long long)n * y;
+      vn[k] = make_int2(y, n);
+      py[k] = make_longlong2(pn, pyv);
+      hist[y] = (int32_t)k;
+      ++k;
+    }
+  }
+  dc_sync<CL>();
+}
+
+// (v, j) of the t-th distinct value of all criteria
+static __device__ __forceinline__ void diff_item(const Ctx& c, int t, int& v, int& j) {
+  v = 0;
+  while (t >= c.dD[v]) {
+    t -= c.dD[v];
+    ++v;
+  }
+  j = t;
+}
+
+// columns: S_j and I_j of every distinct value of every criterion, one warp
+// per value (the data center's warps take the values round-robin, so each
+// warp gets small and large j alike).  The lanes add n_i R(y_j - y_i) over
+// the values at least two below y_j; the linear part comes from the prefix
+// sums.  F = 1 needs no column sums (L2 = 1).
+template <int B, bool CL>
+static __device__ void diff_columns(const Sm& s, const InstDev& I) {
+  const Ctx& c = *s.c;
+  constexpr int NW = B / 32;
+  const int lane = lane_id(), H = c.H;
+  const int TW = c.ncta * NW, gw = c.rank * NW + (int)(threadIdx.x >> 5);
+  int Dt = 0;
+  for (int v = 0; v < c.C; ++v) Dt += c.dD[v];
+  const long long F = c.n;
+  for (int t = gw; t < Dt; t += TW) {
+    int v, j;
+    diff_item(c, t, v, j);
+    const int2* vn = I.dx_vn + (size_t)v * H;
+    const int2 e = vn[j];
+    const int yj = e.x;
+    const int nb1 = (j > 0 && vn[j - 1].x == yj - 1) ? vn[j - 1].y : 0;  // n(y_j - 1)
+    const int lo = j - (nb1 ? 1 : 0);
+    u64 alo = 0, ahi = 0;
+    for (int i = lane; i < lo; i += 32) {
+      const int2 q = vn[i];
+      const u64 r = recip_q64(I.recip, yj - q.x);
+      add128(alo, ahi, r * (u64)q.y, __umul64hi(r, (u64)q.y));
+    }
+    warp_sum128(alo, ahi);
+    if (lane == 0) {
+      const longlong2 p = I.dx_py[(size_t)v * H + j];
+      // sum_{i>j} n_i (y_i - y_j) + n_j + n(y_j - 1), times 2^64
+      const long long lin = (c.S1[v] - p.y) - (long long)yj * (F - p.x) + e.y + nb1;
+      ahi += (u64)lin;
+      const double sj = __dmul_rn(u128_to_double(alo, ahi), 0x1p-64);
+      const double inv = __ddiv_rn(1.0, sj);
+      I.dx_I[(size_t)v * H + j] = __double2ull_rn(__dmul_rn(inv, 0x1p64));
+    }
+  }
+  dc_sync<CL>();
+}
+
+// prefix, criterion v: exclusive 128-bit prefix sums P1_j = sum_{i<j} n_i I_i
+// and P2_j = sum_{i<j} n_i y_i I_i, the distinct values split between the
+// blocks and threads in order like the bins of diff_compact.
+template <int B, bool CL>
+static __device__ void diff_prefix(const Sm& s, const InstDev& I, int v) {
+  const Ctx& c = *s.c;
+  const int H = c.H, tid = threadIdx.x;
+  const long long D = c.dD[v];
+  const int j0 = (int)(D * c.rank / c.ncta), j1 = (int)(D * (c.rank + 1) / c.ncta);
+  const long long nb = j1 - j0;
+  const int t0 = j0 + (int)(nb * tid / B), t1 = j0 + (int)(nb * (tid + 1) / B);
+  const int2* vn = I.dx_vn + (size_t)v * H;
+  const u64* Iv = I.dx_I + (size_t)v * H;
+  auto terms = [&](int j, u64* a) {  // n_j I_j and n_j y_j I_j
+    const int2 e = vn[j];
+    const u64 Ij = Iv[j];
+    a[0] = Ij * (u64)e.y;
+    a[1] = __umul64hi(Ij, (u64)e.y);
+    a[2] = a[0];
+    a[3] = a[1];
+    mul128_32(a[2], a[3], (u64)e.x);
+  };
+  u64 w[4] = {0, 0, 0, 0};
+  for (int j = t0; j < t1; ++j) {
+    u64 a[4];
+    terms(j, a);
+    add128(w[0], w[1], a[0], a[1]);
+    add128(w[2], w[3], a[2], a[3]);
+  }
+  u64 ex[4], tot[4];
+  block_scan4<B, true>(s, w, ex, tot);
+  cluster_offsets<CL, true>(s, tot);
+  u64 p[4] = {c.doff[0], c.doff[1], c.doff[2], c.doff[3]};
+  add128(p[0], p[1], ex[0], ex[1]);
+  add128(p[2], p[3], ex[2], ex[3]);
+  ulonglong2* P = I.dx_P + 2 * (size_t)v * H;
+  for (int j = t0; j < t1; ++j) {
+    P[2 * j] = make_ulonglong2(p[0], p[1]);
+    P[2 * j + 1] = make_ulonglong2(p[2], p[3]);
+    u64 a[4];
+    terms(j, a);
+    add128(p[0], p[1], a[0], a[1]);
+    add128(p[2], p[3], a[2], a[3]);
+  }
+  dc_sync<CL>();
+}
+
+// rows: T_i and the local priority L2_i of every distinct value, one warp
+// per value; the lanes add n_j floor((R(y_j - y_i) I_j + 2^63) / 2^64) over
+// the values at least two above y_i, the rest comes from the prefix sums.
+template <int B, bool CL>
+static __device__ void diff_rows(const Sm& s, const InstDev& I) {
+  const Ctx& c = *s.c;
+  constexpr int NW = B / 32;
+  const int lane = lane_id(), H = c.H;
+  const int TW = c.ncta * NW, gw = c.rank * NW + (int)(threadIdx.x >> 5);
+  int Dt = 0;
+  for (int v = 0; v < c.C; ++v) Dt += c.dD[v];
+  const long long F = c.n;
+  for (int t = gw; t < Dt; t += TW) {
+    int v, i;
+    diff_item(c, t, v, i);
+    const int D = c.dD[v];
+    const int2* vn = I.dx_vn + (size_t)v * H;
+    const u64* Iv = I.dx_I + (size_t)v * H;
+    const int2 e = vn[i];
+    const int yi = e.x;
+    const bool a1 = i + 1 < D && vn[i + 1].x == yi + 1;  // the value y_i + 1 is present
+    u64 alo = 0, ahi = 0;
+    if (F > 1)
+      for (int j = i + (a1 ? 2 : 1) + lane; j < D; j += 32) {
+        const int2 q = vn[j];
+        const u64 Ij = Iv[j];
+        const u64 r = recip_q64(I.recip, q.x - yi);
+        const u64 plo = r * Ij, phi = __umul64hi(r, Ij);
+        const u64 term = phi + (plo >> 63);
+        add128(alo, ahi, term * (u64)q.y, __umul64hi(term, (u64)q.y));
+      }
+    warp_sum128(alo, ahi);
+    if (lane == 0) {
+      double l2 = 1.0;
+      if (F > 1) {
+        const ulonglong2* P = I.dx_P + 2 * ((size_t)v * H + i);
+        const ulonglong2 p1 = P[0], p2 = P[1];
+        u64 llo = p1.x, lhi = p1.y;
+        mul128_32(llo, lhi, (u64)yi);  // y_i P1_i - P2_i >= 0
+        sub128(llo, lhi, p2.x, p2.y);
+        const u64 Ii = Iv[i];
+        add128(llo, lhi, Ii * (u64)e.y, __umul64hi(Ii, (u64)e.y));
+        if (a1) {
+          const u64 In = Iv[i + 1], nn = (u64)vn[i + 1].y;
+          add128(llo, lhi, In * nn, __umul64hi(In, nn));
+        }
+        add128(alo, ahi, llo, lhi);
+        l2 = __ddiv_rn(__dmul_rn(u128_to_double(alo, ahi), 0x1p-64), (double)F);
+      }
+      I.dx_val[(size_t)v * H + i] = l2;
+    }
+  }
+  dc_sync<CL>();
+}
+
+// priority: PG = sum_v L1_v L2_v (in criterion order, each step one IEEE
+// operation) of this block's viable hosts, -1 for the others; then, once
+// every block has looked its values up, the bins used are cleared.
+template <int B, bool CL>
+static __device__ void diff_priority(const Sm& s, const InstDev& I) {
+  const Ctx& c = *s.c;
+  const int H = c.H, C = c.C;
+  for (int u = c.h0 + threadIdx.x; u < c.h1; u += B) {
+    const int x0 = I.dx_x[u];
+    double pg = -1.0;
+    if (x0 >= 0) {
+      pg = 0.0;
+      for (int v = 0; v < C; ++v) {
+        const int xv = v == 0 ? x0 : I.dx_x[v * H + u];
+        const int k = I.dx_hist[I.dx_hoff[v] + xv];
+        pg = __dadd_rn(pg, __dmul_rn(c.L1[v], I.dx_val[(size_t)v * H + k]));
+      }
+    }
+    I.dx_pg[u] = pg;
+  }
+  dc_sync<CL>();
+  int Dt = 0;
+  for (int v = 0; v < C; ++v) Dt += c.dD[v];
+  for (int t = c.rank * B + threadIdx.x; t < Dt; t += c.ncta * B) {
+    int v, j;
+    diff_item(c, t, v, j);
+    I.dx_hist[I.dx_hoff[v] + I.dx_vn[(size_t)v * H + j].x] = 0;
+  }
+}
+
+// a5' under AHP DIFF: the global priority of every host of this block into
+// I.dx_pg (-1: not viable), all phases above.  All threads of every block of
+// the data center call it; ends with a block barrier.
+template <int B, bool CL>
+static __device__ void diff_priorities(const Sm& s, const InstDev& I) {
+  const Ctx& c = *s.c;
+  if (c.n == 0) return;  // no viable host: nothing to rank (pick_diff checks c.n)
+  diff_hist<B>(s, I);
+  dc_sync<CL>();
+  for (int v = 0; v < c.C; ++v) diff_compact<B, CL>(s, I, v);
+  if (c.n > 1) {
+    diff_columns<B, CL>(s, I);
+    for (int v = 0; v < c.C; ++v) diff_prefix<B, CL>(s, I, v);
+  }
+  diff_rows<B, CL>(s, I);
+  diff_priority<B, CL>(s, I);
+  __syncthreads();
+}
+
+// a6 under AHP DIFF: exact FP64 argmax (lowest index on ties) over the
+// viable hosts whose commit can succeed and that did not fail one; in a
+// cluster each block takes its own hosts and the blocks' results are
+// combined in rank order.  Sets c.winner (-1: none), c.wscore and c.xw.
+template <int B, bool CL>
 static __device__ void pick_diff(const Sm& s, const InstDev& I) {
   Ctx& c = *s.c;
   const int tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
   constexpr int NW = B / 32;
   Sel64 b = {-1.0, INT_MAX};
-  for (int p = tid; p < c.nvc; p += B) {
-    const int u = I.dx_idx[p];
-    if (!((s.trymask[u % B] >> (u / B)) & 1u) && commit_possible<B>(s, u))
-      b = sel64_combine(b, Sel64{I.dx_pg[p], u});
-  }
+  if (c.n > 0)
+    for (int u = c.h0 + tid; u < c.h1; u += B) {
+      const double pg = I.dx_pg[u];
+      if (pg >= 0.0 && !((s.trymask[u % B] >> (u / B)) & 1u) && commit_possible<B>(s, u))
+        b = sel64_combine(b, Sel64{pg, u});
+    }
   for (int o = 16; o > 0; o >>= 1) {
     Sel64 q = {__shfl_xor_sync(0xffffffffu, b.s, o), __shfl_xor_sync(0xffffffffu, b.idx, o)};
     b = sel64_combine(b, q);
@@ -1683,11 +2110,36 @@ static __device__ void pick_diff(const Sm& s, const InstDev& I) {
       t = sel64_combine(t, q);
     }
     if (lane == 0) {
-      c.winner = t.s < 0.0 ? -1 : t.idx;
-      c.wscore = t.s;
-      if (t.s >= 0.0) host_crit_slow<B>(s, t.idx, c.xw);
+      if (CL) {
+        c.xs.s64 = t.s;
+        c.xs.idx64 = t.idx;
+      } else {
+        c.winner = t.s < 0.0 ? -1 : t.idx;
+        c.wscore = t.s;
+      }
     }
   }
+  if (CL) {
+    cl_sync();
+    if (w == 0) {
+      Sel64 t = {-1.0, INT_MAX};
+      if (lane < c.ncta) {
+        const Xch* R = cl_map(&c.xs, lane);
+        t = Sel64{R->s64, R->idx64};
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        Sel64 q = {__shfl_xor_sync(0xffffffffu, t.s, o), __shfl_xor_sync(0xffffffffu, t.idx, o)};
+        t = sel64_combine(t, q);
+      }
+      if (lane == 0) {
+        c.winner = t.s < 0.0 ? -1 : t.idx;
+        c.wscore = t.s;
+      }
+    }
+  }
+  __syncthreads();
+  // the winner's criteria (its decision record), from the pass of diff_hist
+  if (tid < kMaxC && c.winner >= 0) c.xw[tid] = tid < c.C ? I.dx_x[tid * c.H + c.winner] : 0;
   __syncthreads();
 }
 
@@ -2185,14 +2637,14 @@ static __device__ bool decide_pod(const Sm& s, const InstDev& I, int g, Pre& nxt
   if (!c.fit) {
     if (c.npe > 0) tables<B>(s, I);  // ends with a barrier
     column_stats<B, CL>(s);
-    if (c.diff) diff_scores<B>(s, I);
+    if (c.diff) diff_priorities<B, CL>(s, I);
   }
   bool placed = false;
   for (;;) {
     if (c.fit)
       pick_fit<B, CL>(s);
     else if (c.diff)
-      pick_diff<B>(s, I);
+      pick_diff<B, CL>(s, I);
     else
       pick_host<B, CL>(s);
     if (c.winner < 0) break;
@@ -2503,12 +2955,12 @@ __global__ void __launch_bounds__(B, 1) k_rank(const InstDev* __restrict__ inst,
                           : __longlong_as_double(0x7ff8000000000000ll);
   }
   if (c.diff) {
-    diff_scores<B>(s, I);
-    for (int p = threadIdx.x; p < c.nvc; p += B) {
-      const int u = I.dx_idx[p];
-      s64[u] = I.dx_pg[p];
-      s32[u] = (float)I.dx_pg[p];
-    }
+    diff_priorities<B, false>(s, I);
+    for (int u = threadIdx.x; u < c.H; u += B)
+      if (feas[u]) {
+        s64[u] = I.dx_pg[u];
+        s32[u] = (float)I.dx_pg[u];
+      }
   }
   if (c.fit) {
     // viable hosts under the capacity-only rule

@@ -65,8 +65,47 @@ struct PodLog {
   double score;  // AHP DIFF: the exact global priority of the chosen host
 };
 
+DC_HD inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
 // Reciprocals round(2^64 / m) for 2 <= m < kRecipTable (AHP DIFF).
 constexpr int32_t kRecipTable = 1 << 16;
+
+// AHP DIFF scratch of one instance (global memory, one contiguous
+// allocation): per host the criteria of the pod being ranked ([C][H], -1 in
+// criterion 0 for a host that is not viable) and its global priority; per
+// criterion the sorted distinct values with their counts ([C][H] int2), the
+// inclusive prefix sums of the counts and of count * value ([C][H]
+// longlong2), the fixed-point inverse column sums I_j ([C][H]), the
+// exclusive prefix sums of n_j I_j and n_j y_j I_j (128-bit each, [C][H]
+// ulonglong2 pairs), the local priorities ([C][H] double); and one histogram
+// per criterion indexed by the value (bins 0..max value: host_cpu, host_mem,
+// 1, link_mbps, link_mbps and, for the locality criterion, 6 x the most peer
+// links of one pod).  The histograms must be zero between decisions.
+constexpr int32_t kDiffMinC5Links = 4096;  // c5 bins for at least this many peer links
+struct DiffLayout {
+  size_t x, pg, vn, py, I, P, val, hist, total;
+  int32_t hoff[kMaxC + 1];  // first bin of criterion v; hoff[C] = bins
+};
+DC_HD inline DiffLayout diff_layout(int H, int C, int host_cpu, int host_mem, int link_mbps,
+                                    int c5_links) {
+  DiffLayout L{};
+  const size_t h = (size_t)H, c = (size_t)kMaxC;
+  size_t o = 0;
+  L.x = o; o = align_up(o + 4 * c * h, 16);
+  L.pg = o; o = align_up(o + 8 * h, 16);
+  L.vn = o; o = align_up(o + 8 * c * h, 16);
+  L.py = o; o = align_up(o + 16 * c * h, 16);
+  L.I = o; o = align_up(o + 8 * c * h, 16);
+  L.P = o; o = align_up(o + 32 * c * h, 16);
+  L.val = o; o = align_up(o + 8 * c * h, 16);
+  const int32_t range[kMaxC] = {host_cpu + 1, host_mem + 1, 2, link_mbps + 1, link_mbps + 1,
+                                6 * (c5_links > kDiffMinC5Links ? c5_links : kDiffMinC5Links) + 1};
+  L.hoff[0] = 0;
+  for (int v = 0; v < kMaxC; ++v) L.hoff[v + 1] = L.hoff[v] + (v < C ? range[v] : 0);
+  L.hist = o; o = align_up(o + 4 * (size_t)L.hoff[kMaxC], 16);
+  L.total = o;
+  return L;
+}
 
 // Everything one instance's thread block needs, in global memory.
 struct InstDev {
@@ -108,13 +147,17 @@ struct InstDev {
   int32_t *sim_start, *sim_head, *sim_next;
   int4* scr_pe;       // peer links of the pod being placed
   PodLog* scr_log;    // [pods of the current request]
-  // AHP DIFF scratch, [H] each (null for the other methods): viable host
-  // list, criteria of the viable hosts [C][H], inverse column sums (Q64),
-  // global priorities; and the shared reciprocal table
-  int32_t* dx_idx;
-  int32_t* dx_val;
-  unsigned long long* dx_inv;
+  // AHP DIFF scratch (see DiffLayout; null for the other methods) and the
+  // shared reciprocal table
+  int32_t* dx_x;
   double* dx_pg;
+  int2* dx_vn;
+  longlong2* dx_py;
+  unsigned long long* dx_I;
+  ulonglong2* dx_P;
+  double* dx_val;
+  int32_t* dx_hist;
+  int32_t dx_hoff[kMaxC];
   const unsigned long long* recip;
   // optional: host-mapped progress word of this data center, written after
   // every operation (operations done) and, once the block has stored the
@@ -125,7 +168,6 @@ struct InstDev {
   unsigned long long* counters;
 };
 
-DC_HD inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 // Shared-memory layout of one scheduling block (bytes), see dc_kernels.cu.
 struct SmemLayout {

@@ -159,9 +159,10 @@ struct dc_t {
   // memory, so the host reads it after a stream synchronisation without a copy
   int32_t* h_err = nullptr;
   int32_t* d_err = nullptr;
-  // AHP DIFF scratch (one allocation): host list [H], criteria [C][H],
-  // inverse column sums [H] (u64), global priorities [H] (f64)
+  // AHP DIFF scratch (one allocation, see DiffLayout); its histogram of the
+  // locality criterion covers pods of up to dx_c5_links peer links
   unsigned char* d_dx = nullptr;
+  int32_t dx_c5_links = 0;
   const unsigned long long* d_recip = nullptr;
   // fat-trees too large for one block's shared memory keep the packed state
   // (cm[H], ctr[H], link slots) in this global scratch
@@ -260,8 +261,7 @@ int launch_shape(const dc_t* d, int block, int ncta, LaunchCfg* out) {
   if (max_hosts_per_thread(block) == 0 || ncta < 1 || ncta > kMaxCluster) return DC_E_INVAL;
   // one 32-bit mask word per thread tracks the hosts of a pod's neighbours
   if (d->H > 32 * block) return DC_E_INVAL;
-  const bool diff = d->cfg.method == DC_AHP && d->cfg.pair_rule == DC_PAIR_DIFF;
-  if (ncta > 1 && (diff || !cluster_block_ok(block) || d->k % ncta != 0)) return DC_E_INVAL;
+  if (ncta > 1 && (!cluster_block_ok(block) || d->k % ncta != 0)) return DC_E_INVAL;
   LaunchCfg L;
   L.block = block;
   L.ncta = ncta;
@@ -335,6 +335,23 @@ int validate_config(const dc_config* c) {
     s += c->weights[v];
   }
   if (!(s > 0.0)) return DC_E_INVAL;
+  return DC_OK;
+}
+
+// AHP DIFF scratch whose locality histogram covers pods of c5_links peer
+// links (allocated or grown in stream order on the instance's stream, the
+// histograms zeroed; the caller makes sure no launch of the instance runs).
+int ensure_diff_scratch(dc_t* d, int32_t c5_links) {
+  if (d->d_dx && c5_links <= d->dx_c5_links) return DC_OK;
+  const int32_t want = std::max(c5_links, kDiffMinC5Links);
+  const DiffLayout X = diff_layout(d->H, d->cfg.n_criteria, d->cfg.host_cpu, d->cfg.host_mem,
+                                   d->cfg.link_mbps, want);
+  unsigned char* q = nullptr;
+  if (cudaMallocAsync((void**)&q, X.total, d->stream) != cudaSuccess) return DC_E_NOMEM;
+  DC_CUDA(cudaMemsetAsync(q + X.hist, 0, X.total - X.hist, d->stream));
+  if (d->d_dx) DC_CUDA(cudaFreeAsync(d->d_dx, d->stream));
+  d->d_dx = q;
+  d->dx_c5_links = want;
   return DC_OK;
 }
 
@@ -490,6 +507,7 @@ int stage(dc_t* d) {
     DC_TRY(d->d_scr_log.ensure(std::max<size_t>(1, d->max_pods), 0, st));
     d->scr_pods = (int32_t)d->d_scr_log.cap;
   }
+  if (d->d_dx) DC_TRY(ensure_diff_scratch(d, d->max_links));
   if (R > d->staged) {
     const int64_t c0 = d->st_c, e0 = d->st_e, l0 = d->st_l;
     const int64_t nc = d->tot_c - c0, ne = d->tot_e - e0, nl = d->tot_l - l0;
@@ -548,11 +566,18 @@ InstDev make_desc(dc_t* d, const int32_t* d_ops, int n_ops, unsigned long long* 
   I.scr_pe = d->d_scr_pe.p;
   I.scr_log = d->d_scr_log.p;
   if (d->d_dx) {
-    const size_t H = (size_t)d->H;
-    I.dx_idx = reinterpret_cast<int32_t*>(d->d_dx);
-    I.dx_val = reinterpret_cast<int32_t*>(d->d_dx + 4 * H);
-    I.dx_inv = reinterpret_cast<unsigned long long*>(d->d_dx + 4 * H * (1 + kMaxC));
-    I.dx_pg = reinterpret_cast<double*>(d->d_dx + 4 * H * (1 + kMaxC) + 8 * H);
+    const DiffLayout X = diff_layout(d->H, d->cfg.n_criteria, d->cfg.host_cpu, d->cfg.host_mem,
+                                     d->cfg.link_mbps, d->dx_c5_links);
+    unsigned char* b = d->d_dx;
+    I.dx_x = reinterpret_cast<int32_t*>(b + X.x);
+    I.dx_pg = reinterpret_cast<double*>(b + X.pg);
+    I.dx_vn = reinterpret_cast<int2*>(b + X.vn);
+    I.dx_py = reinterpret_cast<longlong2*>(b + X.py);
+    I.dx_I = reinterpret_cast<unsigned long long*>(b + X.I);
+    I.dx_P = reinterpret_cast<ulonglong2*>(b + X.P);
+    I.dx_val = reinterpret_cast<double*>(b + X.val);
+    I.dx_hist = reinterpret_cast<int32_t*>(b + X.hist);
+    for (int v = 0; v < kMaxC; ++v) I.dx_hoff[v] = X.hoff[v];
   }
   I.recip = d->d_recip;
   I.state_global = d->state_global ? 1 : 0;
@@ -740,9 +765,7 @@ int dc_create(const dc_config* cfg, void* cuda_stream, dc_t** out) {
           cudaSuccess)
     rc = DC_E_NOMEM;
   if (rc == DC_OK && cfg->method == DC_AHP && cfg->pair_rule == DC_PAIR_DIFF) {
-    // 4 + 4C + 8 + 8 bytes per host (4-byte sections first keep 8-byte alignment)
-    if (cudaMalloc((void**)&d->d_dx, (size_t)H * (4 + 4 * kMaxC + 16)) != cudaSuccess)
-      rc = DC_E_NOMEM;
+    rc = ensure_diff_scratch(d, kDiffMinC5Links);
     if (rc == DC_OK) rc = recip_table(d->stream, &d->d_recip);
   }
   if (rc == DC_OK) rc = launch_weights(cfg->n_criteria, cfg->pair_rule, d->d_W, d->d_L1, d->stream);
@@ -1565,6 +1588,11 @@ int dc_rank_hosts(dc_t* d, const dc_request* q, int32_t pod, const int32_t* host
   float* d_s32 = nullptr;
   double* d_s64 = nullptr;
   InstDev* d_desc = nullptr;
+  if (rc == DC_OK && d->d_dx) {
+    // the instance's AHP DIFF histograms must cover this request's pods
+    settle(d, true);
+    rc = ensure_diff_scratch(d, tmp.max_links);
+  }
   if (rc == DC_OK) rc = stage(&tmp);
   if (rc == DC_OK &&
       (cudaMalloc((void**)&d_host_of, std::max(1, r.n_c) * 4) != cudaSuccess ||
@@ -1582,6 +1610,7 @@ int dc_rank_hosts(dc_t* d, const dc_request* q, int32_t pod, const int32_t* host
     tmp.d_err = d->d_err;
     tmp.h_err = d->h_err;
     tmp.d_dx = d->d_dx;
+    tmp.dx_c5_links = d->dx_c5_links;
     tmp.d_recip = d->d_recip;
     tmp.state_global = d->state_global;
     tmp.d_gstate = d->d_gstate;

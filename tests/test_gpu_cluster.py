@@ -152,8 +152,8 @@ def test_cluster_shape_validation(ds):
     """Shapes that cannot hold the data center are refused."""
     with pytest.raises(ds.DcError):
         ds.set_launch(16, 6, W.TOPSIS, W.RATIO, 256, 3)  # 3 does not divide k
-    with pytest.raises(ds.DcError):
-        ds.set_launch(16, 6, W.AHP, W.DIFF, 256, 2)  # AHP DIFF stays on one block
+    ds.set_launch(16, 6, W.AHP, W.DIFF, 256, 2)  # AHP DIFF runs on clusters too
+    ds.set_launch(16, 6, W.AHP, W.DIFF, 0, 1)
     with pytest.raises(ds.DcError):
         ds.set_launch(48, 6, W.TOPSIS, W.RATIO, 512, 8)  # 27,648 hosts > 32 x 512
     with pytest.raises(ds.DcError):
@@ -189,3 +189,42 @@ def test_autotune_keeps_state_and_results(ds, stream):
     finally:
         for inst in wl.instances[1:3]:
             ds.set_launch(inst.k, inst.n_criteria, inst.method, inst.pair_rule, 0, 1)
+
+
+@pytest.mark.parametrize("k,block,ncta", [(8, 256, 2), (16, 256, 4), (16, 512, 8)])
+def test_cluster_ahp_diff(ds, stream, launch, k, block, ncta):
+    """AHP with the difference rule over a cluster: the histograms, the
+    distinct-value lists and their prefix sums are split between the blocks
+    (offsets through distributed shared memory), the column and row sums
+    between all warps of the cluster."""
+    inst = W.k16(k=k, n_requests=30 if k == 8 else 15, method=W.AHP, pair_rule=W.DIFF).instances[0]
+    dc = _run(ds, stream, launch, inst, block, ncta)
+    check_instance(dc, inst, where="cluster diff k%d %dx%d" % (k, ncta, block))
+
+
+def test_k48_ahp_diff(ds, stream, launch):
+    """AHP DIFF on the paper-scale fat-tree (k = 48, 27,648 hosts) with the
+    k48 workload's requests (pods of 1-8, Pareto bandwidths) and 1 Gbps
+    links (pre-load scaled from the workload's 40 Gbps one), so that the
+    oracle's plain sums over all pairs of the ~1,000 distinct bandwidth
+    values stay fast: one block and clusters of 4 and 16 blocks against one
+    oracle run, every request and the final state."""
+    import dataclasses
+
+    from parity_util import gpu_results
+
+    base = W.k48(n_requests=4, method=W.AHP, pair_rule=W.DIFF).instances[0]
+    pre_link = (base.pre_link.astype(np.int64) * 1000 // 40000).astype(np.int32)
+    inst = dataclasses.replace(base, link_mbps=1000, pre_link=pre_link)
+    runs = []
+    for block, ncta in ((1024, 1), (1024, 16), (1024, 4)):
+        dc = _run(ds, stream, launch, inst, block, ncta)
+        runs.append(((block, ncta),) + gpu_results(dc, inst.reqs.n))
+        dc.close()
+    ref, odc = O.run_instance(inst)
+    assert sum(r["status"] == O.ACCEPTED for r in ref) >= 1
+    for shape, got, state in runs:
+        for r in range(len(ref)):
+            assert_same_result(got[r], ref[r], "k48 diff %s req %d" % (shape, r))
+        for f, g in state.items():
+            assert np.array_equal(g, odc.state(f)), ("k48 diff state", shape, f)

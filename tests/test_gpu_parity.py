@@ -59,8 +59,6 @@ def test_small_intervals_and_pods(ds, stream, seed):
 @pytest.mark.parametrize("k,n_req", [(8, 120), (16, 60)])
 @pytest.mark.parametrize("method,rule", METHODS)
 def test_k16_prefix(ds, stream, k, n_req, method, rule):
-    if rule == W.DIFF:
-        n_req = n_req // 4  # O(F^2) per criterion and decision in both implementations
     inst = W.k16(k=k, n_requests=n_req, method=method, pair_rule=rule).instances[0]
     dc = ds.load_instance(inst, stream=stream)
     ds.schedule([dc])
