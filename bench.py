@@ -59,9 +59,12 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--serving-events", type=int, default=0,
                     help="serving replay: leading timed events to replay (0 = all)")
-    ap.add_argument("--plain-events", type=int, default=3000,
-                    help="serving replay one request per launch: leading events")
+    ap.add_argument("--serving-prefix", type=int, default=20000,
+                    help="serving replay: leading events replayed by both arms (continuous "
+                         "batching and one request per launch)")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-plain", action="store_true",
+                    help="skip the one-request-per-launch run of the workload")
     ap.add_argument("--serving-only", action="store_true",
                     help="only the serving replay (one JSON line); the default run starts it "
                          "as a child process so that it shares no device context with the "
@@ -79,6 +82,14 @@ def parse():
                          "(default: autotuned)")
     ap.add_argument("--largest-only", action="store_true",
                     help="only the k=48 data-center measurement (one JSON line)")
+    ap.add_argument("--no-largest-diff", action="store_true",
+                    help="skip the k=48 AHP difference-rule measurement")
+    ap.add_argument("--diff-requests", type=int, default=2,
+                    help="requests of the k=48 AHP difference-rule data center")
+    ap.add_argument("--diff-shape", default="1024x16",
+                    help="launch shape BLOCKxBLOCKS_PER_DC of the k=48 AHP difference-rule run")
+    ap.add_argument("--largest-diff-only", action="store_true",
+                    help="only the k=48 AHP difference-rule measurement (one JSON line)")
     ap.add_argument("--no-comparators", action="store_true",
                     help="skip the method comparison (TOPSIS, AHP, best fit, worst fit)")
     ap.add_argument("--no-graph", action="store_true",
@@ -118,20 +129,21 @@ def config_dict(args, wl, world):
 # ----------------------------------------------------------------- oracle (CPU)
 
 def oracle_sample(wl, seconds, threads=1):
-    """Runs the FP64 oracle over the first requests (2 on one thread, 8 on
-    several) of instances taken in order (each thread takes the next instance; instances are independent)
-    until `seconds` pass; returns (host_rankings, wall_s, description,
-    requests, threads).  The oracle's C calls release the GIL, so the
-    threads run on separate cores."""
+    """Runs the FP64 oracle over whole FCFS chains (every request of a data
+    center, so the sample covers every position in the chain) of the
+    workload's data centers in their order (which cycles through the fat-tree
+    sizes); each thread takes the next data center while less than `seconds`
+    have passed and finishes the chain it started.  Returns (host_rankings,
+    wall_s, description, requests, threads).  The oracle's C calls release
+    the interpreter lock, so the threads run on separate cores."""
     import concurrent.futures as cf
     import oracle as O
 
     O.build_oracle()
-    per_inst = 2 if threads == 1 else 8  # requests per instance
     t0 = time.perf_counter()
     lock = threading.Lock()
     nxt = [0]
-    tot = {"hr": 0, "reqs": 0, "inst": 0, "ks": set()}
+    tot = {"hr": 0, "reqs": 0, "inst": 0, "ks": {}}
 
     def worker():
         while time.perf_counter() - t0 < seconds:
@@ -142,24 +154,24 @@ def oracle_sample(wl, seconds, threads=1):
                 return
             inst = wl.instances[i]
             dc = O.OracleDC.from_instance(inst)
-            hr = r = 0
-            while r < min(per_inst, inst.reqs.n) and time.perf_counter() - t0 < seconds:
+            hr = 0
+            for r in range(inst.reqs.n):
                 out = dc.schedule(inst.reqs.request(r))
                 hr += out["n_decisions"] * inst.hosts
-                r += 1
             with lock:
                 tot["hr"] += hr
-                tot["reqs"] += r
+                tot["reqs"] += inst.reqs.n
                 tot["inst"] += 1
-                tot["ks"].add(inst.k)
+                tot["ks"][inst.k] = tot["ks"].get(inst.k, 0) + 1
 
     with cf.ThreadPoolExecutor(threads) as ex:
         for f in [ex.submit(worker) for _ in range(threads)]:
             f.result()
     wall = time.perf_counter() - t0
-    desc = ("oracle.c (FP64), %d thread(s) over independent instances: first 1-%d requests of "
-            "%d instances (k=%s), %.1f s" % (threads, per_inst, tot["inst"], sorted(tot["ks"]),
-                                             wall))
+    ks = ", ".join("%d x k=%d" % (n, k) for k, n in sorted(tot["ks"].items()))
+    desc = ("oracle.c (FP64), %d thread(s) over independent data centers: whole %d-request "
+            "chains of %d data centers (%s), %.1f s" % (
+                threads, wl.instances[0].reqs.n, tot["inst"], ks, wall))
     return tot["hr"], wall, desc, tot["reqs"], threads
 
 
@@ -309,8 +321,11 @@ def ncu_traffic(host_rankings_per_launch):
 def run_serving(args, ds, torch):
     """Replays the serving workload (64 k=16 data centers, Poisson arrivals
     at 50k requests/s for 1 s, Zipf(1.1) over the data centers, 2-128
-    containers, exponential lifetimes) through dc_server_replay, with
-    continuous batching and, on a prefix, one request per launch."""
+    containers, exponential lifetimes) through dc_server_replay: continuous
+    batching and one request per launch on the same leading events
+    (--serving-prefix), and continuous batching on all events.  Per data
+    center: requests and p99 latency of the busiest ones (Zipf puts most of
+    the load on a few), which attributes the tail."""
     from paper_1909_07673_gb300 import workloads as W
 
     wl = W.serving()
@@ -326,24 +341,33 @@ def run_serving(args, ds, torch):
         srv.close()
         for d in dcs:
             d.close()
-        L = np.sort(lat[kind == 0]) * 1e3
+        sub = kind == 0
+        L = np.sort(lat[sub]) * 1e3
+        per = []
+        for i in np.argsort(-np.bincount(inst[sub], minlength=len(wl.instances)))[:3]:
+            li = np.sort(lat[sub & (inst == i)]) * 1e3
+            per.append({"instance": int(i), "requests": int(len(li)),
+                        "p50_ms": float(li[len(li) // 2]) if len(li) else None,
+                        "p99_ms": float(li[int(len(li) * 0.99)]) if len(li) else None})
         return {"events": int(len(t)), "requests": int(st["requests"]),
                 "arrival_span_s": float(t[-1]), "wall_s": st["wall_s"],
                 "requests_per_s": st["requests"] / st["wall_s"],
                 "host_rankings_per_s": st["host_rankings"] / st["wall_s"],
                 "launches": int(st["launches"]),
-                "latency_ms": {"p50": float(L[len(L) // 2]), "p99": float(L[int(len(L) * 0.99)])}}
+                "latency_ms": {"p50": float(L[len(L) // 2]), "p99": float(L[int(len(L) * 0.99)])},
+                "busiest_instances": per}
 
-    batched = replay(args.serving_events, 0)
-    plain = replay(args.plain_events, 1)
+    n = args.serving_prefix
     return {
         "workload": "64 k=16 data centers (0-70 %% pre-load), Poisson %d requests/s for 1 s, "
                     "Zipf(1.1) over data centers, 2-128 containers, lifetimes Exp(100 arrivals)"
                     % 50000,
         "latency": "arrival (replayed on the host clock) to completion seen by the host",
-        "continuous_batching": batched,
-        "plain_launch": dict(plain, note="one request per launch, one launch at a time, "
-                                         "first %d events" % plain["events"]),
+        "same_prefix": {"events": n,
+                        "continuous_batching": replay(n, 0),
+                        "plain_launch": dict(replay(n, 1),
+                                             note="one request per launch, one launch at a time")},
+        "continuous_batching_all_events": replay(args.serving_events, 0),
     }
 
 
@@ -539,7 +563,89 @@ def run_largest(args, ds, torch, peak):
     }
 
 
+# ----------------------------------------------------------------- AHP DIFF
+
+SM_COUNT = 152
+LANES_PER_SM = 128  # FP32 lanes per SM
+
+
+def run_largest_diff(args, ds, torch):
+    """AHP with the difference rule on one k=48 data center at the paper's
+    scale (27,648 hosts, 40 Gbps links, 0-100 % pre-load), the first
+    --diff-requests requests of the k48 workload (64-512 containers in pods
+    of 1-8), on one thread-block cluster (state-resetting launches, CUDA
+    events).  The work is the definition's: per decision and criterion, the
+    pairwise column and row sums over the D_v distinct values of the viable
+    hosts, 2 D_v^2 pair evaluations (the kernel counts them); ALU roofline
+    with 4 operations per pair evaluation (difference, comparison /
+    selection, reciprocal, accumulation) against the FP32 lanes of the whole
+    GPU at the sampled clock."""
+    from paper_1909_07673_gb300 import workloads as W
+
+    inst = W.k48(n_requests=args.diff_requests, method=W.AHP, pair_rule=W.DIFF).instances[0]
+    stream = torch.cuda.Stream()
+    b, n = (int(x) for x in args.diff_shape.lower().split("x"))
+    ds.set_launch(inst.k, inst.n_criteria, inst.method, inst.pair_rule, b, n)
+    try:
+        dc = ds.load_instance(inst, stream=stream)
+        plan = ds.Plan([dc], ds.PLAN_RESET)
+        times = []
+        with Clocks(int(os.environ.get("LOCAL_RANK", "0"))) as clk:
+            for rep in range(3):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                plan.launch(stream)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if rep > 0:
+                    times.append(e0.elapsed_time(e1))
+        plan.collect()
+        dec, hr, _, _ = plan.stats()
+        pairs = plan.diff_pairs()
+        block, ncta, _ = ds.get_launch(dc)
+        acc = sum(dc.status(r)[0] == ds.ACCEPTED for r in range(inst.reqs.n))
+        plan.close()
+        dc.close()
+    finally:
+        ds.set_launch(inst.k, inst.n_criteria, inst.method, inst.pair_rule, 0, 1)
+    ms = statistics.mean(times)
+    ck = clk.summary()
+    mhz = ck.get("sm_mhz") or 2070.0
+    peak = SM_COUNT * LANES_PER_SM * mhz * 1e6 / 1e12
+    achieved = 4.0 * pairs / (ms * 1e-3) / 1e12
+    return {
+        "workload": "one k=48 fat-tree (27,648 hosts, 40 Gbps), first %d requests of 64-512 "
+                    "containers in pods of 1-8, AHP difference rule, 6 criteria" % inst.reqs.n,
+        "launch_shape": {"block": block, "blocks_per_dc": ncta},
+        "ms_per_launch": ms, "decisions": dec, "us_per_decision": ms * 1e3 / max(1, dec),
+        "host_rankings_per_s": hr / (ms * 1e-3), "accepted_requests": int(acc),
+        "pair_evaluations": pairs, "pair_evaluations_per_s": pairs / (ms * 1e-3),
+        "pair_evaluations_per_decision": pairs / max(1, dec),
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                     "frac": achieved / peak,
+                     "note": "4 ops per pair evaluation x 2 sum_v D_v^2 pairs per decision; peak "
+                             "= %d SMs x %d FP32 lanes x %.0f MHz (sampled); the data center "
+                             "runs on %d of the %d SMs" % (SM_COUNT, LANES_PER_SM, mhz, ncta,
+                                                           SM_COUNT)},
+        "clocks": ck,
+    }
+
+
 # ----------------------------------------------------------------- ours
+
+def run_largest_diff_only(args):
+    import torch
+
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    import __graft_entry__
+
+    __graft_entry__.build()
+    from paper_1909_07673_gb300 import dcsched as ds
+
+    print(json.dumps({"largest_fat_tree_diff": run_largest_diff(args, ds, torch)}), flush=True)
+    return 0
+
 
 def run_largest_only(args):
     import torch
@@ -574,11 +680,41 @@ def serving_child(args):
     env = {k: v for k, v in os.environ.items()
            if k not in ("RANK", "WORLD_SIZE", "LOCAL_WORLD_SIZE", "GROUP_RANK")}
     cmd = [sys.executable, os.path.abspath(__file__), "--serving-only",
-           "--serving-events", str(args.serving_events), "--plain-events", str(args.plain_events)]
+           "--serving-events", str(args.serving_events), "--serving-prefix",
+           str(args.serving_prefix)]
     r = subprocess.run(cmd, env=env, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("serving replay failed:\n" + r.stderr[-4000:])
     return json.loads(r.stdout.strip().splitlines()[-1])["serving"]
+
+
+def run_plain(args, ds, wl, stream):
+    """The workload scheduled one request per launch (see run_ours)."""
+    dcs = [ds.DataCenter.from_instance(inst, stream=stream) for inst in wl.instances]
+    R = max(inst.reqs.n for inst in wl.instances)
+    lat, hr, n = [], 0, 0
+    t0 = time.perf_counter()
+    for r in range(R):
+        for dc, inst in zip(dcs, wl.instances):
+            if r >= inst.reqs.n:
+                continue
+            dc.submit(inst.reqs.request(r))
+            ds.schedule([dc])
+            st, nd, _ = dc.status(r)
+            lat.append(time.perf_counter() - t0)
+            hr += nd * inst.hosts
+            n += 1
+    wall = time.perf_counter() - t0
+    for dc in dcs:
+        dc.close()
+    lat = np.sort(np.array(lat)) * 1e3
+    return {"requests": n, "wall_s": wall, "requests_per_s": n / wall,
+            "host_rankings_per_s": hr / wall,
+            "latency_ms": {"p50": float(lat[len(lat) // 2]), "p99": float(lat[int(len(lat) * 0.99)])},
+            "note": "every request of the workload, one request per launch (submit, schedule, "
+                    "synchronize, read), round-robin over the data centers; latency = completion "
+                    "time from the start (all requests arrive at the start, as for the batched "
+                    "launch)"}
 
 
 def optional_section(name, fn, *a):
@@ -662,19 +798,12 @@ def run_ours(args):
     (ms_step, ms_kernel), (hr_all, dec_all, req_all, acc_all) = reduce_over_ranks(
         dist, [ms_step, ms_kernel], [hr, dec, n_req, accepted], "cuda")
 
-    # one request per launch on a sample (one instance per size, 8 requests)
-    plain_hr, plain_req, plain_s = 0, 0, 0.0
-    for inst in wl.instances[:4]:
-        dc = ds.DataCenter.from_instance(inst, stream=stream)
-        t = time.perf_counter()
-        for r in range(min(8, inst.reqs.n)):
-            dc.submit(inst.reqs.request(r))
-            ds.schedule([dc])
-            st, nd, _ = dc.status(r)
-            plain_hr += nd * inst.hosts
-            plain_req += 1
-        plain_s += time.perf_counter() - t
-        dc.close()
+    # one request per launch on the same workload: every request of every
+    # data center arrives at the start, and each is submitted, scheduled alone
+    # (one launch) and read back before the next; round-robin over the data
+    # centers, each data center's requests in FCFS order; latency = completion
+    # time from the start, as for the batched launch
+    plain = None if args.no_plain else run_plain(args, ds, wl, stream)
 
     # end to end through the C-ABI with host buffers: submit every request
     # (host copies; the data centers are independent, so a pool of host
@@ -719,6 +848,8 @@ def run_ours(args):
     traffic = ncu_traffic(hr)
     largest = None if args.no_largest else optional_section(
         "largest_fat_tree", run_largest, args, ds, torch, peak)
+    largest_diff = None if (args.no_largest_diff or rank != 0) else optional_section(
+        "largest_fat_tree_diff", run_largest_diff, args, ds, torch)
     comparators = None if (args.no_comparators or rank != 0) else optional_section(
         "comparators", run_comparators, args, ds, torch)
     graph = None if (args.no_graph or rank != 0) else optional_section(
@@ -755,10 +886,7 @@ def run_ours(args):
         "accepted_fraction": acc_all / req_all,
         "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[int(len(lat) * 0.99)],
                        "note": "request completion time from the start of the batched launch"},
-        "plain_launch": {"host_rankings_per_s": plain_hr / plain_s,
-                         "requests_per_s": plain_req / plain_s,
-                         "sample": "one request per launch (submit, schedule, sync, read) on the "
-                                   "first 8 requests of one instance per fat-tree size"},
+        "plain_launch": plain,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                 "d2h_bytes_per_step": int(d2h), "submit_threads": n_submit},
         "gpu_launches": args.steps * nkern,
@@ -776,6 +904,8 @@ def run_ours(args):
         line["serving"] = serving
     if largest is not None:
         line["largest_fat_tree"] = largest
+    if largest_diff is not None:
+        line["largest_fat_tree_diff"] = largest_diff
     if comparators is not None:
         line["comparators"] = comparators
     if graph is not None:
@@ -794,6 +924,8 @@ def main():
         return run_reference(args)
     if args.largest_only:
         return run_largest_only(args)
+    if args.largest_diff_only:
+        return run_largest_diff_only(args)
     if args.serving_only:
         return run_serving_only(args)
     return run_ours(args)

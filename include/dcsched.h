@@ -251,6 +251,13 @@ int dc_plan_collect(dc_plan* plan);
 int dc_plan_stats(dc_plan* plan, int64_t* decisions, int64_t* host_rankings,
                   int32_t* kernels_per_launch, int64_t* start_ns);
 
+/* AHP DIFF work of the last collected launch: 2 * sum_v D_v^2 summed over
+ * its pod decisions, D_v the distinct values of criterion v among the
+ * viable hosts (the pairwise column and row sums of Sec. V-B, Eqs. 9-10, over
+ * distinct values); 0 for the other methods.  No counterpart in the paper
+ * (accounting of the measurement). */
+int dc_plan_diff_pairs(dc_plan* plan, int64_t* pairs);
+
 /* Bytes copied host -> device (request inputs) and device -> host (results)
  * by this instance since dc_create.  No counterpart in the paper
  * (accounting of the end-to-end measurement). */
@@ -359,8 +366,9 @@ int dc_get_launch(const dc_t* dc, int32_t* block, int32_t* ncta, int64_t* smem_b
  * current shapes; a candidate replaces the current shape when it is at
  * least 3 % faster.  Only the first max_ops operations of every instance
  * run in a trial (0: all); the shapes found that way are then timed on all
- * queued operations against the starting shapes and kept only when at least
- * 1 % faster.  Blocking.  The instances' state and queues are
+ * queued operations against the starting shapes (alternately, best of
+ * three each, every timing a graph-captured launch) and kept only when at
+ * least 2 % faster.  Blocking.  The instances' state and queues are
  * as before the call (their device state is saved and restored).  Writes
  * one entry per kind, up to max_out, and the number of kinds to *n_out. */
 typedef struct {

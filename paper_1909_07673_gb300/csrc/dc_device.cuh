@@ -114,6 +114,9 @@ struct Ctx {
   int32_t n_over, h_over;  // neighbour hosts whose uplink cannot carry their links
   int32_t only_host;       // -1: any host may commit, -2: none, else only that host
   uint32_t bwt32;          // bw_total clamped to 2^31 (above every link residual)
+  // the fields above still have to be computed for the current pod, on the
+  // state after the previous pod's commit (done during column_stats)
+  int32_t uplink_pending;
   // column statistics over the viable hosts
   int32_t n;
   long long S1[kMaxC], S2[kMaxC];
@@ -162,6 +165,9 @@ struct Sm {
   int32_t* ctr;   // [H] container count | kPreBit
   int32_t* lk;    // link residuals, layout of link_slots()
   int32_t *T1, *T1h, *T2, *S1, *S1h, *S2, *Be;  // [E] per edge switch
+  // [E] per edge switch, what a host there that holds none of the pod's
+  // neighbours needs: {T1, c5 | (S1 < 0) << 31}
+  int2* Er;
   int32_t* Cp;    // [k] per pod
   uint32_t* tmark;    // [B] bit j of word t: host t + j*B hosts a neighbour
   uint32_t* trymask;  // [B] bit j of word t: host t + j*B failed a commit
@@ -198,6 +204,7 @@ static __device__ __forceinline__ Sm carve(unsigned char* base, const InstDev& I
   int32_t* t = reinterpret_cast<int32_t*>(base + L.tab);
   s.T1 = t; s.T1h = t + E; s.T2 = t + 2 * E; s.S1 = t + 3 * E; s.S1h = t + 4 * E;
   s.S2 = t + 5 * E; s.Be = t + 6 * E;
+  s.Er = reinterpret_cast<int2*>(base + L.er);
   s.Cp = reinterpret_cast<int32_t*>(base + L.cp);
   s.tmark = reinterpret_cast<uint32_t*>(base + L.tmark);
   s.trymask = reinterpret_cast<uint32_t*>(base + L.trymask);
@@ -368,15 +375,25 @@ static __device__ __forceinline__ bool host_crit(const Sm& s, int u, int32_t* x,
   x[3] = up;
   int c4 = up, c5 = 0;
   if (c.npe > 0) {
-    const int e = div_half(c, u), p = div_half(c, e);
-    const int Tx = (isp && s.T1h[e] == u) ? s.T2[e] : s.T1[e];
-    const int Sx = (isp && s.S1h[e] == u) ? s.S2[e] : s.S1[e];
-    const int Nx = (isp && c.need1h == u) ? c.need2 : c.need1;
-    f = f && up >= Nx && Sx >= 0;
-    c4 = (Tx == kInf) ? c.link_mbps : imin(up, Tx);
-    const int A = isp ? peer_links_on(s, u) : 0;
-    const int Bn = s.Be[e], Cn = s.Cp[p];
-    c5 = 6 * A + 4 * (Bn - A) + 2 * (Cn - Bn);
+    const int e = div_half(c, u);
+    if (!isp) {
+      // the edge switch's record: T1, and the locality with the sign bit set
+      // when the slack S1 is negative
+      const int2 r = s.Er[e];
+      f = f && up >= c.need1 && r.y >= 0;
+      c4 = (r.x == kInf) ? c.link_mbps : imin(up, r.x);
+      c5 = r.y & 0x7fffffff;
+    } else {
+      const int p = div_half(c, e);
+      const int Tx = s.T1h[e] == u ? s.T2[e] : s.T1[e];
+      const int Sx = s.S1h[e] == u ? s.S2[e] : s.S1[e];
+      const int Nx = c.need1h == u ? c.need2 : c.need1;
+      f = f && up >= Nx && Sx >= 0;
+      c4 = (Tx == kInf) ? c.link_mbps : imin(up, Tx);
+      const int A = peer_links_on(s, u);
+      const int Bn = s.Be[e], Cn = s.Cp[p];
+      c5 = 6 * A + 4 * (Bn - A) + 2 * (Cn - Bn);
+    }
   }
   if (CC == 6 || (CC == 0 && c.C == 6)) {
     x[4] = c4;
@@ -717,6 +734,17 @@ static __device__ __forceinline__ void peer_entry(const Sm& s, bool byhost, int 
   }
 }
 
+// The per-edge-switch record of a host that holds none of the pod's
+// neighbours: its c4 bound T1, and its locality 4 Be + 2 (Cp - Be) (links
+// to neighbours under the same edge switch, in the same pod) with the sign
+// bit set when the smallest slack S1 is negative (not viable).
+static __device__ __forceinline__ int2 edge_record(const Sm& s, int e, int t1, int s1) {
+  const Ctx& c = *s.c;
+  const int Bn = s.Be[e], Cn = s.Cp[div_half(c, e)];
+  const int c5 = 4 * Bn + 2 * (Cn - Bn);
+  return make_int2(t1, c5 | (s1 < 0 ? (int)0x80000000u : 0));
+}
+
 // a2/a3 tables: T'_v[e] = min(uplink(v), best switch-path bottleneck from
 // edge switch e to edge(v)) folded over the pod's placed neighbours v (one
 // entry per neighbour host, see peer_entry; the top-2 folds give the same
@@ -742,6 +770,18 @@ static __device__ void build_tables(const Sm& s) {
     Top2 tt = {kInf, -1, kInf}, sl = {kInf, -1, kInf};
     const bool byhost = c.hash_ok;
     const int nent = byhost ? c.nhash : c.npe;
+    // this lane's own links (aggregation switch p*half + a to every core,
+    // edge switch e to every aggregation switch) are the same for every
+    // neighbour: with k / 2 fixed at compile time they stay in registers
+    constexpr int NR = HALF ? HALF : 1;
+    int own_ac[NR], own_ea[NR];
+    if (HALF) {
+#pragma unroll
+      for (int q = 0; q < NR; ++q) {
+        own_ac[q] = active ? s.lk[s_ac(c, p * half + a, q)] : 0;
+        own_ea[q] = active ? s.lk[s_ea(c, e, q)] : 0;
+      }
+    }
     for (int i = 0; i < nent; ++i) {
       int v, need;
       peer_entry(s, byhost, i, v, need);
@@ -750,14 +790,16 @@ static __device__ void build_tables(const Sm& s) {
       if (active && p != pv) {
 #pragma unroll
         for (int cc = 0; cc < half; ++cc)
-          gm = imax(gm, imin(s.lk[s_ac(c, p * half + a, cc)], s.lk[s_ac(c, pv * half + a, cc)]));
+          gm = imax(gm, imin(HALF ? own_ac[HALF ? cc : 0] : s.lk[s_ac(c, p * half + a, cc)],
+                             s.lk[s_ac(c, pv * half + a, cc)]));
       }
       int mid = -1;
 #pragma unroll
       for (int a2 = 0; a2 < half; ++a2) {
         const int g2 = __shfl_sync(0xffffffffu, gm, gbase + a2);
         if (active) {
-          int m = imin(s.lk[s_ea(c, e, a2)], s.lk[s_ea(c, ev, a2)]);
+          int m = imin(HALF ? own_ea[HALF ? a2 : 0] : s.lk[s_ea(c, e, a2)],
+                       s.lk[s_ea(c, ev, a2)]);
           if (p != pv) m = imin(m, g2);
           mid = imax(mid, m);
         }
@@ -772,6 +814,7 @@ static __device__ void build_tables(const Sm& s) {
     if (active) {
       s.T1[e] = tt.v1; s.T1h[e] = tt.h1; s.T2[e] = tt.v2;
       s.S1[e] = sl.v1; s.S1h[e] = sl.h1; s.S2[e] = sl.v2;
+      s.Er[e] = edge_record(s, e, tt.v1, sl.v1);
     }
   }
   __syncthreads();
@@ -843,6 +886,11 @@ static __device__ void build_tables_wide(const Sm& s) {
     }
     __syncthreads();
   }
+  for (int el = tid; el < ne; el += B) {
+    const int e = e0 + el;
+    s.Er[e] = edge_record(s, e, s.T1[e], s.S1[e]);
+  }
+  __syncthreads();
 }
 
 // Tables of this block's pods: the wide passes for a global state when the
@@ -939,6 +987,13 @@ static __device__ void column_stats(const Sm& s) {
   }
   if (lane == 0) s.red32[w * (2 * kMaxC + 1) + 2 * kMaxC] = (int)wc;
   __syncthreads();
+  // the commit prefilter of this pod, deferred from the previous commit, by
+  // the last warp (idle in the pass below when it has no criterion); its
+  // fields are read only from the candidate scan on, after the final barrier
+  if (!CL && w == NW - 1 && c.uplink_pending) {
+    pod_uplink_check_warp(s);
+    if (lane == 0) c.uplink_pending = 0;
+  }
   // block level: warp w reduces criteria w, w + NW, ... over the NW partials
   for (int v = w; v < C; v += NW) {
     long long a = 0, b = 0;
@@ -2071,6 +2126,13 @@ static __device__ void diff_priorities(const Sm& s, const InstDev& I) {
   diff_hist<B>(s, I);
   dc_sync<CL>();
   for (int v = 0; v < c.C; ++v) diff_compact<B, CL>(s, I, v);
+  if (I.counters && c.rank == 0 && threadIdx.x == 0) {
+    // the definition's work: every (i, j) pair of distinct values, once for
+    // the column sums and once for the row sums
+    unsigned long long pairs = 0;
+    for (int v = 0; v < c.C; ++v) pairs += 2ull * (unsigned long long)c.dD[v] * c.dD[v];
+    atomicAdd(&I.counters[3], pairs);
+  }
   if (c.n > 1) {
     diff_columns<B, CL>(s, I);
     for (int v = 0; v < c.C; ++v) diff_prefix<B, CL>(s, I, v);
@@ -2147,10 +2209,16 @@ static __device__ void pick_diff(const Sm& s, const InstDev& I) {
 // the result).  Ties: lowest aggregation index a, then lowest core index c.
 // links[] receive global link ids.
 struct PathSel { int b, idx; };
-static __device__ __forceinline__ PathSel path_combine(PathSel a, PathSel b) {
-  if (a.b > b.b) return a;
-  if (a.b < b.b) return b;
-  return {a.b, imin(a.idx, b.idx)};
+
+// Packed candidate key of the path search: bottleneck b (a residual, below
+// 2^21) above, 1023 - candidate index (index < 1024: at most (k/2)^2 = 576
+// candidates) below, so that the largest key has the largest bottleneck and,
+// among equal ones, the lowest index; 0 means no candidate.
+static __device__ __forceinline__ unsigned path_key(int b, int idx) {
+  return ((unsigned)b << 10) | (unsigned)(1023 - idx);
+}
+static __device__ __forceinline__ PathSel path_unkey(unsigned key) {
+  return PathSel{(int)(key >> 10), 1023 - (int)(key & 1023u)};
 }
 
 static __device__ int widest_path_warp(const Sm& s, int hs, int ht, int* links, int* nl) {
@@ -2163,23 +2231,22 @@ static __device__ int widest_path_warp(const Sm& s, int hs, int ht, int* links, 
     links[0] = hs; links[1] = ht; *nl = 2;
     return imin(us, ut);
   }
-  PathSel best = {-1, INT_MAX};
   const bool same_pod = ps == pt;
   const int ncand = same_pod ? half : half * half;
   // candidate j takes aggregation a = j mod half and core cc = j div half, so
   // that consecutive lanes read consecutive link slots; its index for the
-  // tie-break is a * half + cc
+  // tie-break is a * half + cc.  The largest bottleneck, then the lowest
+  // index, is the maximum of one packed key (one warp redux)
+  unsigned key = 0;
   for (int j = lane; j < ncand; j += 32) {
     const int cc = same_pod ? 0 : div_half(c, j), a = j - cc * half;
     int b = imin(imin(us, ut), imin(s.lk[s_ea(c, es, a)], s.lk[s_ea(c, et, a)]));
     if (!same_pod)
       b = imin(b, imin(s.lk[s_ac(c, ps * half + a, cc)], s.lk[s_ac(c, pt * half + a, cc)]));
-    best = path_combine(best, PathSel{b, same_pod ? a : a * half + cc});
+    key = max(key, path_key(b, same_pod ? a : a * half + cc));
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    PathSel q = {__shfl_xor_sync(0xffffffffu, best.b, o), __shfl_xor_sync(0xffffffffu, best.idx, o)};
-    best = path_combine(best, q);
-  }
+  key = __reduce_max_sync(0xffffffffu, key);
+  const PathSel best = path_unkey(key);
   const int a = same_pod ? best.idx : div_half(c, best.idx), cc = same_pod ? 0 : best.idx - a * half;
   if (same_pod) {
     links[0] = hs; links[1] = l_ea(c, es, a); links[2] = l_ea(c, et, a); links[3] = ht;
@@ -2209,28 +2276,22 @@ static __device__ int widest_path_block(const Sm& s, int hs, int ht, int* links,
     links[0] = hs; links[1] = ht; *nl = 2;
     return imin(us, ut);
   }
-  PathSel best = {-1, INT_MAX};
   const bool same_pod = ps == pt;
   const int ncand = same_pod ? half : half * half;
+  unsigned key = 0;  // see path_key
   for (int j = tid; j < ncand; j += B) {
     const int cc = same_pod ? 0 : div_half(c, j), a = j - cc * half;
     int b = imin(imin(us, ut), imin(s.lk[s_ea(c, es, a)], s.lk[s_ea(c, et, a)]));
     if (!same_pod)
       b = imin(b, imin(s.lk[s_ac(c, ps * half + a, cc)], s.lk[s_ac(c, pt * half + a, cc)]));
-    best = path_combine(best, PathSel{b, same_pod ? a : a * half + cc});
+    key = max(key, path_key(b, same_pod ? a : a * half + cc));
   }
-  for (int o = 16; o > 0; o >>= 1) {
-    PathSel q = {__shfl_xor_sync(0xffffffffu, best.b, o), __shfl_xor_sync(0xffffffffu, best.idx, o)};
-    best = path_combine(best, q);
-  }
-  PathSel* ws = reinterpret_cast<PathSel*>(s.sel);
-  if (lane == 0) ws[w] = best;
+  key = __reduce_max_sync(0xffffffffu, key);
+  unsigned* ws = reinterpret_cast<unsigned*>(s.sel);
+  if (lane == 0) ws[w] = key;
   __syncthreads();
-  best = lane < NW ? ws[lane] : PathSel{-1, INT_MAX};
-  for (int o = 16; o > 0; o >>= 1) {
-    PathSel q = {__shfl_xor_sync(0xffffffffu, best.b, o), __shfl_xor_sync(0xffffffffu, best.idx, o)};
-    best = path_combine(best, q);
-  }
+  key = __reduce_max_sync(0xffffffffu, lane < NW ? ws[lane] : 0u);
+  const PathSel best = path_unkey(key);
   const int a = same_pod ? best.idx : div_half(c, best.idx), cc = same_pod ? 0 : best.idx - a * half;
   if (same_pod) {
     links[0] = hs; links[1] = l_ea(c, es, a); links[2] = l_ea(c, et, a); links[3] = ht;
@@ -2467,6 +2528,7 @@ static __device__ void load_instance(const Sm& s, const InstDev& I) {
     c.ac0 = I.H + I.half * c.ld;
     c.mh = ((1ull << 32) + (unsigned long long)I.half - 1) / (unsigned long long)I.half;
     c.arrive = 0;
+    c.uplink_pending = 0;
     for (int v = 0; v < kMaxC; ++v) {
       c.W[v] = v < I.C ? I.W[v] : 0.0;
       c.L1[v] = v < I.C ? I.L1[v] : 0.0;
@@ -2602,9 +2664,13 @@ static __device__ void after_commit_warp(const Sm& s, const InstDev& I, int g, P
         c.dmax_cpu = c.dmax_cpu_n;
         c.dmax_mem = c.dmax_mem_n;
         c.nfail = 0;
+        // the prefilter's uplink check reads the state after this commit; no
+        // phase before the candidate scan uses it, so it runs beside the
+        // column statistics (c.fit has none: run it now)
+        c.uplink_pending = c.fit ? 0 : 1;
       }
       __syncwarp();
-      pod_uplink_check_warp(s);
+      if (c.fit) pod_uplink_check_warp(s);
     } else {
       set_pod_hosts(s, I, g, u);
       pod_clear_warp<B>(s);

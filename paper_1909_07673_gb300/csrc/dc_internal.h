@@ -164,14 +164,15 @@ struct InstDev {
   // state back, set to n_ops + 1 (system-scope release)
   int32_t* progress;
   int32_t* err;       // [1] 0 or a DC_E_* code
-  // [3] pod decisions, host rankings (accumulated), launch start clock (min)
+  // [4] pod decisions, host rankings (accumulated), launch start clock
+  // (min), AHP DIFF pair evaluations 2 sum_v D_v^2 (accumulated)
   unsigned long long* counters;
 };
 
 
 // Shared-memory layout of one scheduling block (bytes), see dc_kernels.cu.
 struct SmemLayout {
-  size_t ctx, cm, ctr, lk, tab, cp, tmark, trymask, hkey, hcnt, hused, hsum, hneed, red64, red32, sel;
+  size_t ctx, cm, ctr, lk, tab, er, cp, tmark, trymask, hkey, hcnt, hused, hsum, hneed, red64, red32, sel;
   size_t st_pc, st_pe, st_hof, pel, curc, pel2, curc2, xwarp, wide, total;
 };
 
@@ -195,6 +196,7 @@ DC_HD inline SmemLayout smem_layout(int k, int block, size_t ctx_bytes, bool sta
   L.ctr = o; o = align_up(o + 4 * H, 16);
   L.lk = o; o = align_up(o + (state_smem ? 4 * link_slots(k) : 0), 16);
   L.tab = o; o = align_up(o + 7 * 4 * E, 16);
+  L.er = o; o = align_up(o + 8 * E, 16);
   L.cp = o; o = align_up(o + 4 * (size_t)k, 16);
   L.tmark = o; o = align_up(o + 4 * (size_t)block, 16);
   L.trymask = o; o = align_up(o + 4 * (size_t)block, 16);

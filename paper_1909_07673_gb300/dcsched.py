@@ -109,6 +109,7 @@ def lib():
         L.dc_plan_launch.argtypes = [C.c_void_p, C.c_void_p]
         L.dc_plan_collect.argtypes = [C.c_void_p]
         L.dc_plan_stats.argtypes = [C.c_void_p, _i64p, _i64p, _i32p, _i64p]
+        L.dc_plan_diff_pairs.argtypes = [C.c_void_p, _i64p]
         L.dc_plan_destroy.argtypes = [C.c_void_p]
         L.dc_plan_destroy.restype = None
         L.dc_simulate.argtypes = [C.c_void_p, C.c_int32, _i32p, _i32p, _i32p]
@@ -344,6 +345,13 @@ class Plan:
         _check(lib().dc_plan_stats(self.h, C.byref(d), C.byref(hr), C.byref(kc), C.byref(t0)),
                "dc_plan_stats")
         return d.value, hr.value, kc.value, t0.value
+
+    def diff_pairs(self) -> int:
+        """AHP DIFF pair evaluations (2 sum_v D_v^2 over the decisions) of the
+        last collected launch (dc_plan_diff_pairs)."""
+        n = C.c_int64()
+        _check(lib().dc_plan_diff_pairs(self.h, C.byref(n)), "dc_plan_diff_pairs")
+        return n.value
 
     def close(self):
         if getattr(self, "h", None) and _lib is not None:
