@@ -183,6 +183,7 @@ struct Sm {
   int4 *curc, *curc2;  // [32] two container-record buffers
   int32_t* xwarp;  // [B / 32][kMaxC + 1] criteria of each warp's leader, mixed flag
   int32_t *wg, *wm;  // [E] each: wide table passes (global-state data centers)
+  int4* rec;         // [H] per-host record of the statistics scan (or null)
 };
 
 static __device__ __forceinline__ Sm carve(unsigned char* base, const InstDev& I, int B) {
@@ -226,6 +227,7 @@ static __device__ __forceinline__ Sm carve(unsigned char* base, const InstDev& I
   s.xwarp = reinterpret_cast<int32_t*>(base + L.xwarp);
   s.wg = reinterpret_cast<int32_t*>(base + L.wide);
   s.wm = s.wg + E;
+  s.rec = I.rec;
   return s;
 }
 
@@ -348,6 +350,20 @@ static __device__ __forceinline__ bool commit_possible(const Sm& s, int u, bool 
     if (slot >= 0) on_u = s.hsum[slot];
   }
   return (long long)s.lk[u] >= c.bw_total - on_u;
+}
+// The same with u's uplink residual already at hand.
+template <int B>
+static __device__ __forceinline__ bool commit_possible_up(const Sm& s, int u, bool isp, int up) {
+  const Ctx& c = *s.c;
+  if (c.npe == 0 || !c.hash_ok) return true;
+  if (c.only_host != -1 && c.only_host != u) return false;
+  if (!isp) return (uint32_t)up >= c.bwt32;
+  long long on_u = 0;
+  {
+    const int slot = peer_slot(s, u);
+    if (slot >= 0) on_u = s.hsum[slot];
+  }
+  return (long long)up >= c.bw_total - on_u;
 }
 template <int B>
 static __device__ __forceinline__ bool commit_possible(const Sm& s, int u) {
@@ -911,6 +927,15 @@ static __device__ __forceinline__ void tables(const Sm& s, const InstDev& I) {
   }
 }
 
+// Per-host record of the statistics scan, read back by the candidate scan
+// of the same decision instead of recomputing the criteria: {free CPU | free
+// memory << 16, uplink residual (below 2^21) | active flag << 22 | viable
+// << 23 | holds a neighbour << 24, c4, c5}.
+static __device__ __forceinline__ int4 host_record(const int32_t* x, bool f, bool isp) {
+  return make_int4(x[0] | (x[1] << 16), x[3] | (x[2] << 22) | (f ? 1 << 23 : 0) | (isp ? 1 << 24 : 0),
+                   x[4], x[5]);
+}
+
 // The host scan of column_stats: this thread's viable hosts folded into its
 // count, sums, sums of squares and extremes (CC: criteria count fixed at
 // compile time, 0: c.C).
@@ -923,7 +948,10 @@ static __device__ __forceinline__ void stats_scan(const Sm& s, uint32_t& cnt, ui
   const uint32_t tmw = s.tmark[(c.h0 + tid) % B];  // u % B is fixed for this thread
   auto visit = [&](int u) {
     int32_t x[kMaxC];
-    if (host_crit<B, CC>(s, u, x, (tmw >> (u / B)) & 1u)) {
+    const bool isp = (tmw >> (u / B)) & 1u;
+    const bool f = host_crit<B, CC>(s, u, x, isp);
+    if (CC == 6 && s.rec) s.rec[u] = host_record(x, f, isp);
+    if (f) {
       ++cnt;
 #pragma unroll
       for (int v = 0; v < kMaxC; ++v) {
@@ -1276,7 +1304,8 @@ static __device__ __forceinline__ unsigned long long f2_fma(unsigned long long a
   return r;
 }
 
-// pick_scan for 6 criteria and TOPSIS, two hosts (u, u + B) per iteration:
+// pick_scan for 6 criteria and TOPSIS (criteria from the statistics scan's
+// records), two hosts (u, u + B) per iteration:
 // their FP32 scores are the scalar score32's operation by operation (x - M
 // as x + (-M), exact for integers below 2^24; products, fused squares and the
 // final sum and quotient rounded the same way), computed in paired lanes;
@@ -1285,7 +1314,7 @@ template <int B, bool CL>
 static __device__ __forceinline__ void pick_scan_pairs(const Sm& s, Lead& me) {
   const Ctx& c = *s.c;
   const int tid = threadIdx.x;
-  const uint32_t tmw = s.tmark[(c.h0 + tid) % B], tyw = s.trymask[(c.h0 + tid) % B];
+  const uint32_t tyw = s.trymask[(c.h0 + tid) % B];
   unsigned long long nM[6], nN[6], Q[6];
 #pragma unroll
   for (int v = 0; v < 6; ++v) {
@@ -1312,19 +1341,41 @@ static __device__ __forceinline__ void pick_scan_pairs(const Sm& s, Lead& me) {
       me.m2 = fmaxf(me.m2, sc);
     }
   };
+  // the criteria come from the statistics scan's records (s.rec); the pair
+  // of the next iteration is loaded while this one is scored
+  auto decode = [](int4 r, int32_t* x, bool& f, bool& isp) {
+    x[0] = r.x & 0xffff;
+    x[1] = (int32_t)((uint32_t)r.x >> 16);
+    x[2] = (r.y >> 22) & 1;
+    x[3] = r.y & 0x3fffff;
+    x[4] = r.z;
+    x[5] = r.w;
+    f = (r.y >> 23) & 1;
+    isp = (r.y >> 24) & 1;
+  };
+  int u = c.h0 + tid;
+  int4 ra = make_int4(0, 0, 0, 0), rb = ra;
+  if (u < c.h1) {
+    ra = s.rec[u];
+    rb = s.rec[u + B < c.h1 ? u + B : u];
+  }
 #pragma unroll 1
-  for (int u = c.h0 + tid; u < c.h1; u += 2 * B) {
+  for (; u < c.h1; u += 2 * B) {
     const int u2 = u + B;
     const bool has2 = u2 < c.h1;
     const int w2 = has2 ? u2 : u;  // in range; its result is then unused
+    int4 na = ra, nb = rb;
+    if (u + 2 * B < c.h1) {
+      na = s.rec[u + 2 * B];
+      nb = s.rec[u + 3 * B < c.h1 ? u + 3 * B : u + 2 * B];
+    }
     int32_t xa[kMaxC], xb[kMaxC];
     const int ja = u / B, jb = w2 / B;
-    const bool ispa = (tmw >> ja) & 1u, ispb = (tmw >> jb) & 1u;
-    // host_crit fills the criteria whatever the outcome
-    const bool ca = host_crit<B, 6>(s, u, xa, ispa);
-    const bool cb = host_crit<B, 6>(s, w2, xb, ispb);
-    const bool oka = ca && !((tyw >> ja) & 1u) && commit_possible<B>(s, u, ispa);
-    const bool okb = cb && !((tyw >> jb) & 1u) && commit_possible<B>(s, w2, ispb);
+    bool ca, cb, ispa, ispb;
+    decode(ra, xa, ca, ispa);
+    decode(rb, xb, cb, ispb);
+    const bool oka = ca && !((tyw >> ja) & 1u) && commit_possible_up<B>(s, u, ispa, xa[3]);
+    const bool okb = cb && !((tyw >> jb) & 1u) && commit_possible_up<B>(s, w2, ispb, xb[3]);
     unsigned long long dp = 0ull, dn = 0ull;
 #pragma unroll
     for (int v = 0; v < 6; ++v) {
@@ -1342,6 +1393,8 @@ static __device__ __forceinline__ void pick_scan_pairs(const Sm& s, Lead& me) {
     const float scb = sb == 0.f ? 1.f : __fdividef(dnb, sb);
     fold(u, oka ? sca : -1.f, xa);
     if (has2) fold(u2, okb ? scb : -1.f, xb);
+    ra = na;
+    rb = nb;
   }
 }
 

@@ -147,6 +147,9 @@ struct InstDev {
   int32_t *sim_start, *sim_head, *sim_next;
   int4* scr_pe;       // peer links of the pod being placed
   PodLog* scr_log;    // [pods of the current request]
+  // [H] per-host records of the statistics scan for the candidate scan of the
+  // same decision (null: not written; the ranking kernel)
+  int4* rec;
   // AHP DIFF scratch (see DiffLayout; null for the other methods) and the
   // shared reciprocal table
   int32_t* dx_x;

@@ -194,6 +194,7 @@ struct dc_t {
   int64_t h2d_bytes = 0, d2h_bytes = 0;
   DevVec<int4> d_scr_pe;
   DevVec<PodLog> d_scr_log;
+  DevVec<int4> d_rec;  // [H] host records of the scheduling kernel
   int32_t scr_links = 0, scr_pods = 0;
   // operations (FCFS) and their progress
   std::vector<int32_t> ops;
@@ -589,6 +590,7 @@ InstDev make_desc(dc_t* d, const int32_t* d_ops, int n_ops, unsigned long long* 
     // each block of a cluster has its own slice of the peer-link scratch
     I.scr_links = (int32_t)(d->d_scr_pe.cap / (size_t)L->ncta);
   }
+  I.rec = d->d_rec.p;
   I.progress = d->progress_slot;
   I.err = d->d_err;
   I.counters = counters;
@@ -764,6 +766,7 @@ int dc_create(const dc_config* cfg, void* cuda_stream, dc_t** out) {
       cudaMalloc((void**)&d->d_gstate, sizeof(int32_t) * (2 * (size_t)H + link_slots(d->k))) !=
           cudaSuccess)
     rc = DC_E_NOMEM;
+  if (rc == DC_OK) rc = d->d_rec.ensure((size_t)H, 0, d->stream);
   if (rc == DC_OK && cfg->method == DC_AHP && cfg->pair_rule == DC_PAIR_DIFF) {
     rc = ensure_diff_scratch(d, kDiffMinC5Links);
     if (rc == DC_OK) rc = recip_table(d->stream, &d->d_recip);
@@ -790,6 +793,7 @@ void dc_destroy(dc_t* d) {
   d->o_tdone.release(st);
   d->d_scr_pe.release(st);
   d->d_scr_log.release(st);
+  d->d_rec.release(st);
   cudaStreamSynchronize(st);
   d->c_lay.release(); d->e_lay.release(); d->p_coff.release(); d->p_eoff.release();
   d->reqs.release();
@@ -1844,6 +1848,7 @@ extern "C" int dc_rank_hosts_static(dc_t* d, const dc_request* q, int32_t pod,
   I.scr_log = reinterpret_cast<PodLog*>(base + L.log);
   I.progress = nullptr;
   I.counters = nullptr;
+  I.rec = nullptr;  // the ranking kernel writes no host records
   cudaStream_t st = d->stream;
   const int32_t n = rec.n_c, m = rec.n_e, P = rec.n_p, H = d->H, C = d->cfg.n_criteria;
   DC_CUDA(cudaMemcpyAsync(base + L.desc, &I, sizeof(I), cudaMemcpyHostToDevice, st));
