@@ -301,19 +301,40 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(host_rankings_per_launch):
-    """DRAM bytes per launch of the scheduling kernel from the committed ncu
-    summary, scaled to this launch's host rankings; None when the summary is
-    missing or was taken on different kernel sources."""
+def ncu_record():
+    """The committed ncu record of the scheduling kernel (DRAM bytes, issue
+    and pipe activity), or None when it is missing or was taken on other
+    kernel sources."""
     p = os.path.join(ROOT, "profiles", "k_schedule_traffic.json")
     try:
         with open(p) as f:
             t = json.load(f)
     except Exception:
         return None
-    if t.get("source_hash") != kernel_source_hash():
+    return t if t.get("source_hash") == kernel_source_hash() else None
+
+
+def ncu_traffic(host_rankings_per_launch):
+    """DRAM bytes per launch of the scheduling kernel from the committed ncu
+    record, scaled to this launch's host rankings; None without a record."""
+    t = ncu_record()
+    if t is None:
         return None
     return t["dram_bytes"] / t["host_rankings"] * host_rankings_per_launch
+
+
+def ncu_pipes():
+    """Issue and pipe activity of the dominant size class from the committed
+    ncu record (fractions of peak on the SMs it runs on), or None."""
+    t = ncu_record()
+    if t is None or "issue_active_pct" not in t:
+        return None
+    return {"class": t["dominant_class"],
+            "issue_active_frac": t["issue_active_pct"] / 100.0,
+            "alu_pipe_frac": t["alu_pipe_active_pct"] / 100.0,
+            "fmaheavy_pipe_frac": t["fmaheavy_pipe_active_pct"] / 100.0,
+            "warp_instructions_per_host_ranking": t["warp_instructions_per_host_ranking"],
+            "source": "profiles/k_schedule_traffic.json (ncu, same kernel sources)"}
 
 
 # ----------------------------------------------------------------- serving
@@ -893,6 +914,7 @@ def run_ours(args):
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "peak_kind": peak_kind + " (STREAM-style copy)",
+                     "pipes": ncu_pipes(),
                      "note": "16 B of host state per host ranking over the scheduling launch "
                              "(graph: state reset + one kernel per fat-tree size)"},
         "cpu_baseline": {"value": cpu_hr / cpu_s, "unit": UNIT, "cores": cpu_threads,
