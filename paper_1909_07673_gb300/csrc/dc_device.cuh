@@ -837,68 +837,113 @@ static __device__ void build_tables(const Sm& s) {
 }
 
 // The same tables for a data center whose state lives in global memory,
-// in three block-wide passes per neighbour so that the loads of the link
-// residuals are spread over all threads (one level of memory latency per
-// pass) instead of forming per-lane chains:
+// in three block-wide passes so that the loads of the link residuals are
+// spread over all threads (one level of memory latency per pass) instead of
+// forming per-lane chains:
 //   G[p][a] = max_c min(ac(p, a, c), ac(pod(v), a, c))   for p != pod(v)
 //   M[e]    = max_a min(ea(e, a), ea(edge(v), a) [, G[pod(e)][a]])
 //   T       = min(uplink(v), M[e]) (no switch link when e = edge(v)),
-// folded into the top-2 tables per neighbour entry like build_tables.
-// Only this block's pods [p0, p1).  Ends with a barrier.
+// folded into the top-2 tables like build_tables.  The passes take a batch
+// of neighbour entries at once (as many as the [E] scratch arrays hold for
+// this block's switches), so a batch costs three block barriers whatever its
+// size.  Only this block's pods [p0, p1).  Ends with a barrier.
+constexpr int kWideBatch = 8;
+
 template <int B>
 static __device__ void build_tables_wide(const Sm& s) {
   const Ctx& c = *s.c;
   const int half = c.half, tid = threadIdx.x;
   const int np = c.p1 - c.p0, ne = np * half, nt = ne * half;
   const int e0 = c.p0 * half;
+  const bool byhost = c.hash_ok;
+  const int nent = byhost ? c.nhash : c.npe;
+  // entries per batch: as many as the [E] scratch arrays hold for this
+  // block's switches, at most kWideBatch (kept in registers below)
+  const int per = imin(kWideBatch, imax(1, c.E / ne));
+  int32_t* ent = s.red32;  // [4][kWideBatch]: host, edge switch, pod, need of the batch
   for (int el = tid; el < ne; el += B) {
     const int e = e0 + el;
     s.T1[e] = kInf; s.T1h[e] = -1; s.T2[e] = kInf;
     s.S1[e] = kInf; s.S1h[e] = -1; s.S2[e] = kInf;
-    s.wg[el] = -1;
-    s.wm[el] = -1;
   }
-  __syncthreads();
-  const bool byhost = c.hash_ok;
-  const int nent = byhost ? c.nhash : c.npe;
-  for (int i = 0; i < nent; ++i) {
-    int v, need;
-    peer_entry(s, byhost, i, v, need);
-    const int ev = div_half(c, v), pv = div_half(c, ev);
-    // pass 1: (pod, aggregation, core) triples of this block; consecutive
-    // threads take consecutive aggregation switches (contiguous link slots,
-    // distinct maxima)
+  for (int b0 = 0; b0 < nent; b0 += per) {
+    const int nb = imin(per, nent - b0);
+    for (int t = tid; t < nb * ne; t += B) {
+      s.wg[t] = -1;
+      s.wm[t] = -1;
+    }
+    if (tid < nb) {
+      int v, need;
+      peer_entry(s, byhost, b0 + tid, v, need);
+      const int ev = div_half(c, v);
+      ent[tid] = v;
+      ent[kWideBatch + tid] = ev;
+      ent[2 * kWideBatch + tid] = div_half(c, ev);
+      ent[3 * kWideBatch + tid] = need;
+    }
+    __syncthreads();
+    // pass 1: (core, pod-local aggregation) pairs of this block, every entry
+    // of the batch; consecutive threads take consecutive aggregation switches
+    // (contiguous link slots, distinct maxima).  The loads of all entries are
+    // issued before the atomics
     for (int t = tid; t < nt; t += B) {
       const int cc = t / ne, pa = t - cc * ne;  // pa = pod-local * half + a
       const int pl = div_half(c, pa), a = pa - pl * half;
       const int p = c.p0 + pl;
-      if (p != pv)
-        atomicMax(&s.wg[pa], imin(s.lk[s_ac(c, p * half + a, cc)], s.lk[s_ac(c, pv * half + a, cc)]));
+      const int own = s.lk[s_ac(c, p * half + a, cc)];
+      int val[kWideBatch];
+#pragma unroll
+      for (int q = 0; q < kWideBatch; ++q) {
+        const int pv = q < nb ? ent[2 * kWideBatch + q] : p;
+        val[q] = pv != p ? imin(own, s.lk[s_ac(c, pv * half + a, cc)]) : -1;
+      }
+#pragma unroll
+      for (int q = 0; q < kWideBatch; ++q)
+        if (val[q] >= 0) atomicMax(&s.wg[q * ne + pa], val[q]);
     }
     __syncthreads();
-    // pass 2: (edge switch, aggregation) pairs of this block, consecutive
+    // pass 2: (aggregation, edge switch) pairs of this block, consecutive
     // threads over consecutive edge switches
     for (int t = tid; t < nt; t += B) {
       const int a = t / ne, el = t - a * ne;
       const int pl = div_half(c, el);
       const int e = e0 + el;
-      int m = imin(s.lk[s_ea(c, e, a)], s.lk[s_ea(c, ev, a)]);
-      if (c.p0 + pl != pv) m = imin(m, s.wg[pl * half + a]);
-      atomicMax(&s.wm[el], m);
+      const int own = s.lk[s_ea(c, e, a)];
+      int val[kWideBatch];
+#pragma unroll
+      for (int q = 0; q < kWideBatch; ++q) {
+        int m = -1;
+        if (q < nb) {
+          m = imin(own, s.lk[s_ea(c, ent[kWideBatch + q], a)]);
+          if (c.p0 + pl != ent[2 * kWideBatch + q]) m = imin(m, s.wg[q * ne + pl * half + a]);
+        }
+        val[q] = m;
+      }
+#pragma unroll
+      for (int q = 0; q < kWideBatch; ++q)
+        if (q < nb) atomicMax(&s.wm[q * ne + el], val[q]);
     }
     __syncthreads();
-    // pass 3: fold per edge switch (one thread per switch), reset the maxima
-    const int up = s.lk[v];
+    // pass 3: fold the batch's entries per edge switch (one thread per
+    // switch; the top-2 folds give the same values in any order)
     for (int el = tid; el < ne; el += B) {
       const int e = e0 + el;
-      const int mid = e == ev ? kInf : s.wm[el];
-      const int T = imin(up, mid);
-      const Top2 tt = min2_combine(Top2{s.T1[e], s.T1h[e], s.T2[e]}, Top2{T, v, kInf});
-      const Top2 sl = min2_combine(Top2{s.S1[e], s.S1h[e], s.S2[e]}, Top2{T - need, v, kInf});
+      int up[kWideBatch];
+#pragma unroll
+      for (int q = 0; q < kWideBatch; ++q) up[q] = q < nb ? s.lk[ent[q]] : 0;
+      Top2 tt = {s.T1[e], s.T1h[e], s.T2[e]}, sl = {s.S1[e], s.S1h[e], s.S2[e]};
+#pragma unroll
+      for (int q = 0; q < kWideBatch; ++q) {
+        if (q < nb) {
+          const int v = ent[q];
+          const int mid = e == ent[kWideBatch + q] ? kInf : s.wm[q * ne + el];
+          const int T = imin(up[q], mid);
+          tt = min2_combine(tt, Top2{T, v, kInf});
+          sl = min2_combine(sl, Top2{T - ent[3 * kWideBatch + q], v, kInf});
+        }
+      }
       s.T1[e] = tt.v1; s.T1h[e] = tt.h1; s.T2[e] = tt.v2;
       s.S1[e] = sl.v1; s.S1h[e] = sl.h1; s.S2[e] = sl.v2;
-      s.wg[el] = -1;
-      s.wm[el] = -1;
     }
     __syncthreads();
   }
