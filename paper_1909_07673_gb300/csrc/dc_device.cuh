@@ -1803,6 +1803,15 @@ static __device__ __forceinline__ void warp_sum128(u64& lo, u64& hi) {
     add128(lo, hi, a, b);
   }
 }
+// acc += a * m exactly (a < 2^64, m < 2^32: a product below 2^96) with two
+// 32 x 32 -> 64-bit multiplies
+static __device__ __forceinline__ void mad128_64x32(u64& lo, u64& hi, u64 a, uint32_t m) {
+  const u64 p0 = (u64)(uint32_t)a * m;          // bits 0..63
+  const u64 p1 = (u64)(uint32_t)(a >> 32) * m;  // bits 32..95
+  const u64 l = p0 + (p1 << 32);
+  const u64 h = (p1 >> 32) + (l < p0 ? 1ull : 0ull);
+  add128(lo, hi, l, h);
+}
 // (hi:lo) * m for m < 2^32, modulo 2^128
 static __device__ __forceinline__ void mul128_32(u64& lo, u64& hi, u64 m) {
   const u64 plo = lo * m, carry = __umul64hi(lo, m);
@@ -2063,10 +2072,10 @@ static __device__ void diff_columns(const Sm& s, const InstDev& I) {
     const int nb1 = (j > 0 && vn[j - 1].x == yj - 1) ? vn[j - 1].y : 0;  // n(y_j - 1)
     const int lo = j - (nb1 ? 1 : 0);
     u64 alo = 0, ahi = 0;
+#pragma unroll 4
     for (int i = lane; i < lo; i += 32) {
       const int2 q = vn[i];
-      const u64 r = recip_q64(I.recip, yj - q.x);
-      add128(alo, ahi, r * (u64)q.y, __umul64hi(r, (u64)q.y));
+      mad128_64x32(alo, ahi, recip_q64(I.recip, yj - q.x), (uint32_t)q.y);
     }
     warp_sum128(alo, ahi);
     if (lane == 0) {
@@ -2152,13 +2161,14 @@ static __device__ void diff_rows(const Sm& s, const InstDev& I) {
     const bool a1 = i + 1 < D && vn[i + 1].x == yi + 1;  // the value y_i + 1 is present
     u64 alo = 0, ahi = 0;
     if (F > 1)
+#pragma unroll 4
       for (int j = i + (a1 ? 2 : 1) + lane; j < D; j += 32) {
         const int2 q = vn[j];
         const u64 Ij = Iv[j];
         const u64 r = recip_q64(I.recip, q.x - yi);
         const u64 plo = r * Ij, phi = __umul64hi(r, Ij);
         const u64 term = phi + (plo >> 63);
-        add128(alo, ahi, term * (u64)q.y, __umul64hi(term, (u64)q.y));
+        mad128_64x32(alo, ahi, term, (uint32_t)q.y);
       }
     warp_sum128(alo, ahi);
     if (lane == 0) {
