@@ -1009,15 +1009,10 @@ static __device__ __forceinline__ void stats_scan(const Sm& s, uint32_t& cnt, ui
       }
     }
   };
-  // the cluster kernel (global state): two hosts in flight hide part of the
-  // L2 latency; the one-block kernel runs faster without unrolling
-  if (CL) {
+  // two hosts in flight hide part of the shared-memory (and, for a global
+  // state, L2) latency of the criteria
 #pragma unroll 2
-    for (int u = c.h0 + tid; u < c.h1; u += B) visit(u);
-  } else {
-#pragma unroll 1
-    for (int u = c.h0 + tid; u < c.h1; u += B) visit(u);
-  }
+  for (int u = c.h0 + tid; u < c.h1; u += B) visit(u);
 }
 
 // a4: exact column statistics over the viable hosts and FP32 constants.
