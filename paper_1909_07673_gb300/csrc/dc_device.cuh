@@ -3031,9 +3031,12 @@ static __device__ void simulate(const Sm& s, const InstDev& I) {
 }
 
 // One data center per thread block (CL = false), or per thread-block cluster
-// of I.ncta blocks (CL = true; cluster index = descriptor index).
+// of I.ncta blocks (CL = true; cluster index = descriptor index).  Blocks of
+// up to 256 threads are compiled for two per SM (at most 128 registers):
+// the small data centers they serve are latency-bound, and a second block
+// on the SM fills its issue slots.
 template <int B, int HPT, bool CL>
-__global__ void __launch_bounds__(B, 1) k_schedule(const InstDev* __restrict__ insts) {
+__global__ void __launch_bounds__(B, (B <= 256 && !CL) ? 2 : 1) k_schedule(const InstDev* __restrict__ insts) {
   extern __shared__ __align__(16) unsigned char smem[];
   const InstDev& I = insts[CL ? cl_id() : (int)blockIdx.x];
   const Sm s = carve(smem, I, B);
