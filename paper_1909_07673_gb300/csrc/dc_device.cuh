@@ -263,6 +263,16 @@ static __device__ __forceinline__ const T* cl_map(const T* p, int rank) {
   asm volatile("mapa.u64 %0, %1, %2;" : "=l"(a) : "l"(p), "r"(rank));
   return reinterpret_cast<const T*>(a);
 }
+// barrier of the first NT threads of a block of B (named barrier 1 when
+// NT < B, the last warp meanwhile working on its own)
+template <int B, int NT>
+static __device__ __forceinline__ void grp_sync() {
+  static_assert(NT % 32 == 0 && NT <= B, "whole warps");
+  if (NT == B)
+    __syncthreads();
+  else
+    asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+}
 static __device__ __forceinline__ int imin(int a, int b) { return a < b ? a : b; }
 static __device__ __forceinline__ int imax(int a, int b) { return a > b ? a : b; }
 static __device__ __forceinline__ int div_half(const Ctx& c, int x) {
@@ -1058,7 +1068,7 @@ static __device__ void column_stats(const Sm& s) {
   // the commit prefilter of this pod, deferred from the previous commit, by
   // the last warp (idle in the pass below when it has no criterion); its
   // fields are read only from the candidate scan on, after the final barrier
-  if (!CL && w == NW - 1 && c.uplink_pending) {
+  if (w == NW - 1 && c.uplink_pending) {
     pod_uplink_check_warp(s);
     if (lane == 0) c.uplink_pending = 0;
   }
@@ -2362,16 +2372,16 @@ static __device__ int widest_path_warp(const Sm& s, int hs, int ht, int* links, 
   return best.b;
 }
 
-// The same search by a whole block (global state: one round of memory
-// latency over all candidates instead of several per lane); every thread
-// gets the result.  The partials live in s.sel, so two calls must be
-// separated by a barrier (the reservation that follows each call ends with
-// one).
-template <int B>
+// The same search by the first NT threads of the block (global state: one
+// round of memory latency over all candidates instead of several per lane);
+// every one of them gets the result.  The partials live in s.sel, so two
+// calls must be separated by a barrier of the group (the reservation that
+// follows each call ends with one).
+template <int B, int NT = B>
 static __device__ int widest_path_block(const Sm& s, int hs, int ht, int* links, int* nl) {
   const Ctx& c = *s.c;
   const int tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
-  constexpr int NW = B / 32;
+  constexpr int NW = NT / 32;
   const int half = c.half;
   const int es = div_half(c, hs), et = div_half(c, ht), ps = div_half(c, es), pt = div_half(c, et);
   const int us = s.lk[hs], ut = s.lk[ht];
@@ -2382,7 +2392,7 @@ static __device__ int widest_path_block(const Sm& s, int hs, int ht, int* links,
   const bool same_pod = ps == pt;
   const int ncand = same_pod ? half : half * half;
   unsigned key = 0;  // see path_key
-  for (int j = tid; j < ncand; j += B) {
+  for (int j = tid; j < ncand; j += NT) {
     const int cc = same_pod ? 0 : div_half(c, j), a = j - cc * half;
     int b = imin(imin(us, ut), imin(s.lk[s_ea(c, es, a)], s.lk[s_ea(c, et, a)]));
     if (!same_pod)
@@ -2392,7 +2402,7 @@ static __device__ int widest_path_block(const Sm& s, int hs, int ht, int* links,
   key = __reduce_max_sync(0xffffffffu, key);
   unsigned* ws = reinterpret_cast<unsigned*>(s.sel);
   if (lane == 0) ws[w] = key;
-  __syncthreads();
+  grp_sync<B, NT>();
   key = __reduce_max_sync(0xffffffffu, lane < NW ? ws[lane] : 0u);
   const PathSel best = path_unkey(key);
   const int a = same_pod ? best.idx : div_half(c, best.idx), cc = same_pod ? 0 : best.idx - a * half;
@@ -2442,9 +2452,9 @@ static __device__ void commit_capacity(const Sm& s, const InstDev& I, int g) {
 // a7/a8: reservations of pod g on c.winner (warp 0 of the block that writes
 // the state and the outputs).  Returns whether the pod is placed; on failure
 // nothing of this attempt stays reserved.
-// BLK: run by the whole block, the path search block-wide (global state);
-// else by warp 0.
-template <int B, bool BLK>
+// BLK: run by the first NT threads of the block, the path search spread
+// over them (global state); else by warp 0.
+template <int B, bool BLK, int NT = B>
 static __device__ bool commit_reserve(const Sm& s, const InstDev& I, int g) {
   Ctx& c = *s.c;
   const int lane = lane_id();
@@ -2468,7 +2478,7 @@ static __device__ bool commit_reserve(const Sm& s, const InstDev& I, int g) {
       L->score = c.wscore;
     }
   }
-  if (BLK) __syncthreads(); else __syncwarp();
+  if (BLK) grp_sync<B, NT>(); else __syncwarp();
   int done = 0;  // peer links committed so far
   bool ok = true;
   for (int base = 0; base < c.npe && ok; base += 32) {
@@ -2488,7 +2498,7 @@ static __device__ bool commit_reserve(const Sm& s, const InstDev& I, int g) {
         if (tid == 0) I.o_bw[c.e_off + e] = bmax;
       } else {
         int links[6], nl = 0;
-        const int b = BLK ? widest_path_block<B>(s, hs, ht, links, &nl)
+        const int b = BLK ? widest_path_block<B, NT>(s, hs, ht, links, &nl)
                           : widest_path_warp(s, hs, ht, links, &nl);
         if (b < bmin) {
           ok = false;
@@ -2507,12 +2517,12 @@ static __device__ bool commit_reserve(const Sm& s, const InstDev& I, int g) {
         if (tid == 0) I.o_bw[c.e_off + e] = amount;
       }
       ++done;
-      if (BLK) __syncthreads(); else __syncwarp();
+      if (BLK) grp_sync<B, NT>(); else __syncwarp();
     }
   }
   if (!ok) {
     // undo this pod's reservations (links committed before the failure)
-    for (int i = BLK ? tid : lane; i < done; i += BLK ? B : 32) {
+    for (int i = BLK ? tid : lane; i < done; i += BLK ? NT : 32) {
       const int e = c.pel[i].x & kLinkIndex;
       int32_t* path = I.o_path + (c.e_off + e) * 6;
       const int bw = I.o_bw[c.e_off + e];
@@ -2523,15 +2533,15 @@ static __device__ bool commit_reserve(const Sm& s, const InstDev& I, int g) {
       }
       I.o_bw[c.e_off + e] = 0;
     }
-    if (BLK) __syncthreads(); else __syncwarp();
+    if (BLK) grp_sync<B, NT>(); else __syncwarp();
     return false;
   }
   if (!BLK || tid < 32) commit_capacity(s, I, g);
-  if (BLK) __syncthreads(); else __syncwarp();
+  if (BLK) grp_sync<B, NT>(); else __syncwarp();
   return true;
 }
 
-// Bookkeeping of every block after the commit of pod g (warp 0): on success
+// Bookkeeping of every block after the commit of pod g (one warp): on success
 // the hosts of the pod's containers, the end of the pod and the set-up of
 // pod g + 1; on failure the winner is masked for the next pick.  Sets
 // c.commit_ok.
@@ -2727,10 +2737,11 @@ static __device__ void set_pod_hosts(const Sm& s, const InstDev& I, int g, int u
   __syncwarp();
 }
 
-// Warp 1 of the one-block shared-memory kernel, while warp 0 commits pod g on
-// the chosen host: ends pod g's neighbour bookkeeping and sets up pod g + 1
-// as if the commit succeeds (the host map, the tables and hashes of the pod
-// are not read by the commit; the fields it reads get the second copy).
+// The set-up warp (warp 1 of the one-block shared-memory kernel, else the
+// last warp of every block) while pod g commits on the chosen host: ends pod
+// g's neighbour bookkeeping and sets up pod g + 1 as if the commit succeeds
+// (the host map, the tables and hashes of the pod are not read by the
+// commit; the fields it reads get the second copy).
 template <int B>
 static __device__ void setup_ahead_warp(const Sm& s, const InstDev& I, int g, Pre& nxt) {
   set_pod_hosts(s, I, g, s.c->winner);
@@ -2739,11 +2750,11 @@ static __device__ void setup_ahead_warp(const Sm& s, const InstDev& I, int g, Pr
   pod_setup_warp<B>(s, I, g + 1, nxt, kSetupAhead);
 }
 
-// Warp 1 after the commit of pod g.  Success: the pod set up ahead becomes
-// the current one (its uplink check runs on the state after the commit), or,
-// without a set-up ahead, pod g ends and pod g + 1 is set up now.  Failure:
-// the host is masked and, after a set-up ahead, pod g's bookkeeping is built
-// again (its failure count kept) for the next pick.
+// The set-up warp after the commit of pod g.  Success: the pod set up ahead
+// becomes the current one (its uplink check runs on the state after the
+// commit), or, without a set-up ahead, pod g ends and pod g + 1 is set up
+// now.  Failure: the host is masked and, after a set-up ahead, pod g's
+// bookkeeping is built again (its failure count kept) for the next pick.
 template <int B>
 static __device__ void after_commit_warp(const Sm& s, const InstDev& I, int g, Pre& nxt,
                                          bool ahead) {
@@ -2817,17 +2828,35 @@ static __device__ bool decide_pod(const Sm& s, const InstDev& I, int g, Pre& nxt
     else
       pick_host<B, CL>(s);
     if (c.winner < 0) break;
-    if (CL) {
-      // the state of a cluster is global: block 0 commits with all its threads
-      if (c.rank == 0) {
-        const bool ok = commit_reserve<B, true>(s, I, g);
-        if (tid == 0) c.xs.ok = ok ? 1 : 0;
+    if (CL || I.state_global) {
+      // global state (one copy for a cluster): all warps of the block but the
+      // last commit pod g (block 0 of a cluster), while the last warp of
+      // every block sets up pod g + 1 ahead; after the barrier that warp
+      // settles the outcome (or, without a set-up ahead, ends pod g)
+      constexpr int NT = B - 32;
+      const bool ahead = g + 1 < c.n_p && c.pel_smem && c.hof_smem;
+      if (tid < NT) {
+        if (!CL || c.rank == 0) {
+          const bool ok = commit_reserve<B, true, NT>(s, I, g);
+          if (tid == 0) c.xs.ok = ok ? 1 : 0;
+        }
+      } else if (ahead) {
+        setup_ahead_warp<B>(s, I, g, nxt);
       }
-      cl_sync();
-      if (tid < 32) commit_finish<B>(s, I, g, nxt, cl_map(&c.xs, 0)->ok != 0);
-    } else if (I.state_global) {
-      const bool ok = commit_reserve<B, true>(s, I, g);
-      if (tid < 32) commit_finish<B>(s, I, g, nxt, ok);
+      if (CL)
+        cl_sync();
+      else
+        __syncthreads();
+      if (tid >= NT) {
+        const bool ok = (CL ? cl_map(&c.xs, 0)->ok : c.xs.ok) != 0;
+        if (ahead) {
+          if (tid == NT) c.commit_ok = ok ? 1 : 0;
+          __syncwarp();
+          after_commit_warp<B>(s, I, g, nxt, true);
+        } else {
+          commit_finish<B>(s, I, g, nxt, ok);
+        }
+      }
     } else {
       // one block, state in shared memory: warp 0 commits pod g while warp 1
       // sets up pod g + 1 ahead; warp 1 then settles the outcome
@@ -2922,7 +2951,8 @@ static __device__ void schedule_request(const Sm& s, const InstDev& I, int r) {
   // the warp that sets up pods (and holds the prefetched records): warp 1 in
   // the one-block shared-memory kernel (it sets up ahead of the commits),
   // warp 0 otherwise
-  const int setup_warp = (!CL && !I.state_global) ? 1 : 0;
+  // the warp that sets pods up (its registers hold the prefetched records)
+  const int setup_warp = (!CL && !I.state_global) ? 1 : B / 32 - 1;
   if ((tid >> 5) == setup_warp && n_p > 0) {
     if (c.pref_regs) nxt = prefetch_pod(c, I, 0);
     pod_setup_warp<B>(s, I, 0, nxt);
