@@ -2374,11 +2374,14 @@ static __device__ int widest_path_warp(const Sm& s, int hs, int ht, int* links, 
 
 // The same search by the first NT threads of the block (global state: one
 // round of memory latency over all candidates instead of several per lane);
-// every one of them gets the result.  The partials live in s.sel, so two
-// calls must be separated by a barrier of the group (the reservation that
-// follows each call ends with one).
+// every one of them gets the result.  When the bottleneck reaches bmin the
+// search also reserves bw^max (bottleneck >= bmax) or bw^min on the chosen
+// links, from the residuals it loaded.  The partials live in s.sel, so two
+// calls must be separated by a barrier of the group (the commit loop ends
+// each link with one, which also publishes the reservation).
 template <int B, int NT = B>
-static __device__ int widest_path_block(const Sm& s, int hs, int ht, int* links, int* nl) {
+static __device__ int widest_path_block(const Sm& s, int hs, int ht, int* links, int* nl,
+                                        int bmin, int bmax) {
   const Ctx& c = *s.c;
   const int tid = threadIdx.x, lane = lane_id(), w = tid >> 5;
   constexpr int NW = NT / 32;
@@ -2387,18 +2390,34 @@ static __device__ int widest_path_block(const Sm& s, int hs, int ht, int* links,
   const int us = s.lk[hs], ut = s.lk[ht];
   if (es == et) {
     links[0] = hs; links[1] = ht; *nl = 2;
-    return imin(us, ut);
+    const int b = imin(us, ut);
+    if (tid == 0 && b >= bmin) {
+      const int amount = b >= bmax ? bmax : bmin;
+      s.lk[hs] = us - amount;
+      s.lk[ht] = ut - amount;
+    }
+    return b;
   }
   const bool same_pod = ps == pt;
   const int ncand = same_pod ? half : half * half;
   unsigned key = 0;  // see path_key
+  int r0 = 0, r1 = 0, r2 = 0, r3 = 0;  // switch-link residuals of this thread's best candidate
   for (int j = tid; j < ncand; j += NT) {
     const int cc = same_pod ? 0 : div_half(c, j), a = j - cc * half;
-    int b = imin(imin(us, ut), imin(s.lk[s_ea(c, es, a)], s.lk[s_ea(c, et, a)]));
-    if (!same_pod)
-      b = imin(b, imin(s.lk[s_ac(c, ps * half + a, cc)], s.lk[s_ac(c, pt * half + a, cc)]));
-    key = max(key, path_key(b, same_pod ? a : a * half + cc));
+    const int x0 = s.lk[s_ea(c, es, a)], x1 = s.lk[s_ea(c, et, a)];
+    int x2 = kInf, x3 = kInf;
+    if (!same_pod) {
+      x2 = s.lk[s_ac(c, ps * half + a, cc)];
+      x3 = s.lk[s_ac(c, pt * half + a, cc)];
+    }
+    const int b = imin(imin(us, ut), imin(imin(x0, x1), imin(x2, x3)));
+    const unsigned k2 = path_key(b, same_pod ? a : a * half + cc);
+    if (k2 > key) {
+      key = k2;
+      r0 = x0; r1 = x1; r2 = x2; r3 = x3;
+    }
   }
+  const unsigned mine = key;
   key = __reduce_max_sync(0xffffffffu, key);
   unsigned* ws = reinterpret_cast<unsigned*>(s.sel);
   if (lane == 0) ws[w] = key;
@@ -2413,6 +2432,19 @@ static __device__ int widest_path_block(const Sm& s, int hs, int ht, int* links,
     links[0] = hs; links[1] = l_ea(c, es, a); links[2] = l_ac(c, ps, a, cc);
     links[3] = l_ac(c, pt, a, cc); links[4] = l_ea(c, et, a); links[5] = ht;
     *nl = 6;
+  }
+  // the thread that evaluated the chosen candidate (keys are distinct) holds
+  // the residuals of all its links: it reserves the amount on them
+  if (mine == key && best.b >= bmin) {
+    const int amount = best.b >= bmax ? bmax : bmin;
+    s.lk[hs] = us - amount;
+    s.lk[ht] = ut - amount;
+    s.lk[s_ea(c, es, a)] = r0 - amount;
+    s.lk[s_ea(c, et, a)] = r1 - amount;
+    if (!same_pod) {
+      s.lk[s_ac(c, ps * half + a, cc)] = r2 - amount;
+      s.lk[s_ac(c, pt * half + a, cc)] = r3 - amount;
+    }
   }
   return best.b;
 }
@@ -2498,7 +2530,7 @@ static __device__ bool commit_reserve(const Sm& s, const InstDev& I, int g) {
         if (tid == 0) I.o_bw[c.e_off + e] = bmax;
       } else {
         int links[6], nl = 0;
-        const int b = BLK ? widest_path_block<B, NT>(s, hs, ht, links, &nl)
+        const int b = BLK ? widest_path_block<B, NT>(s, hs, ht, links, &nl, bmin, bmax)
                           : widest_path_warp(s, hs, ht, links, &nl);
         if (b < bmin) {
           ok = false;
@@ -2511,7 +2543,7 @@ static __device__ bool commit_reserve(const Sm& s, const InstDev& I, int g) {
         for (int j = 0; j < 6; ++j)
           if (tid == j && j < nl) mylink = links[j];
         if (mylink >= 0) {
-          s.lk[lslot(c, mylink)] -= amount;
+          if (!BLK) s.lk[lslot(c, mylink)] -= amount;  // BLK: reserved by the search
           path[tid] = mylink;
         }
         if (tid == 0) I.o_bw[c.e_off + e] = amount;
