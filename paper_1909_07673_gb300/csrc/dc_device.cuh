@@ -254,6 +254,7 @@ static __device__ __forceinline__ int cl_id() {
   return (int)r;
 }
 static __device__ __forceinline__ void cl_sync() {
+  __syncwarp();  // the aligned barrier needs the warp's threads together
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;"
                ::: "memory");
 }
@@ -264,14 +265,19 @@ static __device__ __forceinline__ const T* cl_map(const T* p, int rank) {
   return reinterpret_cast<const T*>(a);
 }
 // barrier of the first NT threads of a block of B (named barrier 1 when
-// NT < B, the last warp meanwhile working on its own)
+// NT < B, the last warp meanwhile working on its own).  The named barrier is
+// the non-aligned form: it follows data-dependent branches of single lanes,
+// after which the threads of a warp need not arrive together (the aligned
+// `bar.sync` requires that); the warp is also reconverged first.
 template <int B, int NT>
 static __device__ __forceinline__ void grp_sync() {
   static_assert(NT % 32 == 0 && NT <= B, "whole warps");
-  if (NT == B)
+  if (NT == B) {
     __syncthreads();
-  else
-    asm volatile("bar.sync 1, %0;" ::"n"(NT) : "memory");
+  } else {
+    __syncwarp();
+    asm volatile("barrier.sync 1, %0;" ::"n"(NT) : "memory");
+  }
 }
 static __device__ __forceinline__ int imin(int a, int b) { return a < b ? a : b; }
 static __device__ __forceinline__ int imax(int a, int b) { return a > b ? a : b; }
