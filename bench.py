@@ -71,8 +71,10 @@ def parse():
                          "batched measurement")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default launch shapes (one block per data center)")
-    ap.add_argument("--tune-ops", type=int, default=20,
-                    help="operations per data center run in each autotuner trial")
+    ap.add_argument("--tune-ops", type=int, default=0,
+                    help="operations per data center run in each autotuner trial (0: all; "
+                         "a prefix of the chains can rank the shapes differently from the "
+                         "whole chains, which set the batched makespan)")
     ap.add_argument("--no-largest", action="store_true",
                     help="skip the single k=48 data-center measurement")
     ap.add_argument("--largest-requests", type=int, default=200,
@@ -891,10 +893,14 @@ def run_ours(args):
             {"k": e["k"], "block": e["block"], "blocks_per_dc": e["ncta"],
              "default": [e["block0"], e["ncta0"]], "trials": e["trials"],
              "kept_after_full_check": e["kept"]} for e in tuned]
-        cfg["autotune"] = ("coordinate descent over launch shapes per fat-tree size, each "
-                           "trial a state-resetting launch of the first %d operations of every "
-                           "data center; the result is kept only if faster than the starting "
-                           "shapes on all operations" % args.tune_ops)
+        cfg["autotune"] = (
+            "coordinate descent over launch shapes per fat-tree size, each trial a "
+            "state-resetting launch of all operations of every data center (the timed "
+            "step's work)" if args.tune_ops <= 0 else
+            "coordinate descent over launch shapes per fat-tree size, each trial a "
+            "state-resetting launch of the first %d operations of every data center; the "
+            "result is kept only if faster than the starting shapes on all operations"
+            % args.tune_ops)
     line = {
         "metric": METRIC, "value": hr_all / (ms_step * 1e-3), "unit": UNIT,
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
