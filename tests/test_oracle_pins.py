@@ -199,6 +199,42 @@ def test_ahp_diff_all_equal_is_uniform():
         assert np.allclose(O.ahp(x, [0.25] * 4, O.DIFF), 1.0 / F, rtol=1e-15)
 
 
+def test_ahp_diff_translation_invariance():
+    """The difference reading (Sec. V-B) compares hosts by x_i - x_j only, so
+    adding a constant to a criterion's column changes no priority (exactly:
+    the differences are integers).  The ratio reading does not have this
+    property, nor would a difference rule with an offset on one side."""
+    rng = np.random.default_rng(6)
+    for _ in range(20):
+        F, C = int(rng.integers(2, 30)), int(rng.choice([4, 6]))
+        x = rng.integers(0, 60, (F, C))
+        w = rng.random(C) + 0.05
+        shift = rng.integers(0, 500, C)
+        assert np.array_equal(O.ahp(x + shift, w, O.DIFF), O.ahp(x, w, O.DIFF))
+    x = np.array([[0, 3], [1, 1], [4, 2]])
+    assert not np.allclose(O.ahp(x + 7, [0.5, 0.5], O.RATIO), O.ahp(x, [0.5, 0.5], O.RATIO))
+
+
+def test_ahp_diff_dominance():
+    """Under the difference reading a_ij grows with x_i - x_j, so a host at
+    least as good as another in every criterion (all benefit criteria) has at
+    least its priority, and strictly more when it is better in a criterion
+    of positive weight and some third host separates them.  A reversed
+    reciprocal (a_ij = 1 / d for d > 0) breaks this."""
+    rng = np.random.default_rng(8)
+    for _ in range(200):
+        F, C = int(rng.integers(2, 20)), int(rng.choice([4, 6]))
+        x = rng.integers(0, 25, (F, C))
+        w = rng.random(C) + 0.05
+        x[0] = np.maximum(x[0], x[1])
+        p = O.ahp(x, w, O.DIFF)
+        assert p[0] >= p[1]
+    # hand case: host 0 better than host 1 in the first criterion only
+    x = np.array([[5, 2], [3, 2], [0, 0]])
+    p = O.ahp(x, [0.5, 0.5], O.DIFF)
+    assert p[0] > p[1] > p[2]
+
+
 def test_ahp_permutation_invariance():
     rng = np.random.default_rng(5)
     x = rng.integers(0, 500, (40, 6))
